@@ -1,0 +1,394 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test names the passage of the paper (or the piece of mathematics) it
+checks.  The CUDA path is not involved.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import adjoint, density, merge, scatter
+from paper_2303_13435_gb300 import inputs
+
+RNG = np.random.default_rng(12345)
+
+
+def _brute_dft_flat(rho):
+    """Eq. 1 as the literal triple sum: one exponential per (voxel, frequency) pair."""
+    n = rho.shape[0]
+    idx = np.indices((n, n, n)).reshape(3, -1)  # (z, y, x) per flat voxel
+    # (k.x) mod N is an exact integer, so the phase is exact up to cos/sin rounding.
+    dot = (idx.T @ idx) % n
+    e = np.exp(-2j * np.pi * dot / n)
+    return (e @ rho.ravel()).reshape(n, n, n) / n ** 3
+
+
+def _brute_dft_axes(rho):
+    """Eq. 1 with the exponential split per axis (exact algebra), direct DFT matrices."""
+    n = rho.shape[0]
+    j = np.arange(n)
+    w = np.exp(-2j * np.pi * ((j[:, None] * j[None, :]) % n) / n)
+    return np.einsum("zyx,cz,by,ax->cba", rho, w, w, w) / n ** 3
+
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10])
+def test_dft3_equals_eq1_triple_sum(n):
+    """Sec. 2.4 Eq. 1: the oracle's FFT equals the literal definition on tiny grids."""
+    rho = RNG.random((n, n, n))
+    F = scatter.dft3(rho)
+    Fb = _brute_dft_flat(rho)
+    assert np.max(np.abs(F - Fb)) <= 1e-12 * np.max(np.abs(Fb))
+
+
+@pytest.mark.parametrize("n", [12, 14, 16])
+def test_dft3_equals_direct_dft_matrices(n):
+    rho = RNG.random((n, n, n))
+    F = scatter.dft3(rho)
+    Fb = _brute_dft_axes(rho)
+    assert np.max(np.abs(F - Fb)) <= 1e-12 * np.max(np.abs(Fb))
+
+
+def test_eq2_separation_with_empty_planes():
+    """Sec. 2.4 Eq. 2: 2D transforms of the nonzero planes, then 1D transforms along the
+    remaining axis with the skipped planes as zeros, give the 3D transform."""
+    n = 12
+    rho = RNG.random((n, n, n))
+    rho[:3] = 0
+    rho[9:] = 0
+    j = np.arange(n)
+    w = np.exp(-2j * np.pi * ((j[:, None] * j[None, :]) % n) / n)
+    planes = {}
+    for z in range(3, 9):
+        planes[z] = (w @ rho[z] @ w.T) / (n * n)   # 2D DFT over (y, x) of plane z
+    F = np.zeros((n, n, n), dtype=complex)
+    for kz in range(n):
+        acc = np.zeros((n, n), dtype=complex)
+        for z, p in planes.items():
+            acc += w[kz, z] * p
+        F[kz] = acc / n
+    assert np.max(np.abs(F - scatter.dft3(rho))) <= 1e-12 * np.max(np.abs(F))
+
+
+def test_dft_at_matches_definition():
+    n = 10
+    rho = RNG.random((n, n, n))
+    rho[:2] = 0
+    ks = np.array([[0, 0, 0], [1, -2, 3], [-5, 4, -1], [2, 2, -5]])
+    Fb = _brute_dft_flat(rho)
+    vals = scatter.dft_at(rho[2:], ks, z_begin=2)
+    for (kx, ky, kz), v in zip(ks, vals):
+        assert abs(v - Fb[kz % n, ky % n, kx % n]) <= 1e-12 * np.abs(Fb).max()
+
+
+def test_parseval():
+    """sum_k |F_k|^2 = (1/N^3) sum_x rho^2 under the 1/N^3 normalisation of Eq. 1."""
+    n = 16
+    rho = RNG.random((n, n, n))
+    I = scatter.intensity(scatter.dft3(rho))
+    assert math.isclose(I.sum(), (rho ** 2).sum() / n ** 3, rel_tol=1e-12)
+
+
+def test_dc_is_electron_count():
+    """F(0) = sum rho / N^3 (Eq. 1), so N^6 I(0) = N_e^2 (Sec. 2.2 electron count)."""
+    n = 16
+    rho = RNG.random((n, n, n))
+    F = scatter.dft3(rho)
+    assert math.isclose(F[0, 0, 0].real * n ** 3, rho.sum(), rel_tol=1e-13)
+    assert math.isclose(scatter.intensity(F)[0, 0, 0] * n ** 6, rho.sum() ** 2, rel_tol=1e-12)
+
+
+def test_tiling_identity():
+    """Sec. 2.3 tiling: an unmasked T-fold tiling of a U^3 cell has F_N(T h) = F_U(h)
+    under Eq. 1 normalisation and F_N(k) = 0 for k not divisible by T."""
+    u, t = 4, 3
+    n = u * t
+    cell = RNG.random((u, u, u)).astype(np.float32)
+    rho = density.tile_mask_density(n, cell, density.ALL).astype(np.float64)
+    FN = scatter.dft3(rho)
+    FU = _brute_dft_flat(cell.astype(np.float64))
+    sub = FN[::t, ::t, ::t]
+    assert np.max(np.abs(sub - FU)) <= 1e-12 * np.abs(FU).max()
+    mask = np.ones_like(FN, dtype=bool)
+    mask[::t, ::t, ::t] = False
+    assert np.max(np.abs(FN[mask])) <= 1e-12 * np.abs(FU).max()
+
+
+# r3(m): number of integer vectors h with |h|^2 = m (sums of three squares; OEIS A005875).
+R3 = {1: 6, 2: 12, 3: 8, 4: 6, 5: 24, 6: 24, 7: 0, 8: 12, 9: 30}
+
+
+def test_bragg_sc_positions_multiplicities_and_intensity():
+    """Simple-cubic Gaussian-atom lattice (a = 1 nm, 16^3 cell tiled 4^3, no mask):
+    intensity only at Q = 2 pi sqrt(m)/a with multiplicity r3(m), each reflection
+    Z^2 exp(-sigma^2 G^2) / U^6 (Fourier transform of a normalised Gaussian)."""
+    ucell, t, a, z, sig = 16, 4, 1.0, 20.0, 0.08
+    n = ucell * t
+    cell = inputs.sc_cell(ucell, a, z, sig)
+    rho = density.tile_mask_density(n, cell, density.ALL).astype(np.float64)
+    I = scatter.intensity(scatter.dft3(rho))
+    k = scatter.signed_freq(n)
+    k2 = (k * k)[:, None, None] + (k * k)[None, :, None] + (k * k)[None, None, :]
+    strong = I > 1e-12 * I.max()
+    for m, mult in R3.items():
+        on_shell = k2 == t * t * m
+        assert int(np.count_nonzero(strong & on_shell)) == mult
+        if mult:
+            g = 2 * math.pi * math.sqrt(m) / a
+            expect = z * z * math.exp(-sig * sig * g * g) / ucell ** 6
+            assert np.allclose(I[on_shell], expect, rtol=2e-6)
+    # nothing off the reciprocal lattice (k divisible by T on every axis)
+    lattice = (k[:, None, None] % t == 0) & (k[None, :, None] % t == 0) & (k[None, None, :] % t == 0)
+    assert I[~lattice].max() <= 1e-20 * I.max()
+    # Q positions through the binning: shells fall into the bins around 2 pi sqrt(m)/a
+    dx = a / ucell
+    for m in (1, 2, 3):
+        q = 2 * math.pi * math.sqrt(m) / a
+        edges = np.array([q * 0.999, q * 1.001])
+        b = scatter.bin_intensity(I, n, dx, edges)
+        assert b["count"][0] == R3[m]
+        assert math.isclose(b["mean_q"][0], q, rel_tol=1e-12)
+
+
+def test_sphere_form_factor():
+    """Uniform voxelised sphere, padded (R <= N dx / 4): binned N^6 <I> follows
+    N_e^2 [3 (sin qR - qR cos qR)/(qR)^3]^2 at low qR (staircase and voxel-sinc
+    deviations of a few percent, Sec. 2.5)."""
+    n, dx = 64, 0.1
+    rvox = 10.0
+    shape = inputs.centred_sphere(n, rvox)
+    cell = np.ones((1, 1, 1), dtype=np.float32)
+    rho = density.tile_mask_density(n, cell, density.SPHERE, shape.center, shape.size).astype(np.float64)
+    ne = rho.sum()
+    reff = (3 * ne / (4 * math.pi)) ** (1 / 3) * dx
+    edges = inputs.linear_edges(inputs.nyquist_q(dx), 64)
+    b = scatter.forward(rho, dx, edges)
+    q = b["mean_q"]
+    x = q * reff
+    th = inputs.sphere_target_curve(q, reff, ne)
+    meas = b["mean"] * n ** 6
+    env = ne ** 2 * np.minimum(1.0, 9.0 / np.maximum(x, 1e-9) ** 4)
+    sel = (x > 0.2) & (x < 8.0) & (b["count"] > 0)
+    assert sel.sum() > 10
+    assert np.all(np.abs(meas[sel] - th[sel]) <= 0.05 * env[sel])
+    low = sel & (x < 2.0)
+    assert np.all(np.abs(meas[low] / th[low] - 1) < 0.03)
+
+
+def test_bin_counts_match_integer_lattice_enumeration():
+    """Sec. 2.5 binning: with edges placed at dq*sqrt(t + 1/2) (never on a lattice shell),
+    n_j is the number of integer vectors k in the grid with t_j < k^2 < t_j+1."""
+    n, dx = 10, 0.2
+    dq = 2 * math.pi / (n * dx)
+    ts = [0, 1, 2, 4, 7, 12, 20, 33, 50, 74]
+    edges = np.array([dq * math.sqrt(t + 0.5) for t in ts])
+    b = scatter.bin_intensity(np.ones((n, n, n)), n, dx, edges)
+    ks = range(-(n // 2), n - n // 2)
+    counts = [0] * (len(ts) - 1)
+    for kx in ks:
+        for ky in ks:
+            for kz in ks:
+                s = kx * kx + ky * ky + kz * kz
+                for j in range(len(ts) - 1):
+                    if ts[j] < s <= ts[j + 1]:
+                        counts[j] += 1
+    assert list(b["count"]) == counts
+    assert np.allclose(b["mean"][np.array(counts) > 0], 1.0)
+
+
+def test_bin_edge_conventions():
+    e = np.array([1.0, 2.0, 4.0])
+    q = np.array([0.5, 1.0, 1.999, 2.0, 4.0, 4.0000001])
+    assert list(scatter.bin_of_q(q, e)) == [-1, 0, 0, 1, 1, -1]
+
+
+def test_sem_definition():
+    """SEM = std (ddof 1) / sqrt(n) within a bin (Sec. 2.5 standard error on the mean)."""
+    n, dx = 8, 0.5
+    dq = 2 * math.pi / (n * dx)
+    I = RNG.random((n, n, n))
+    edges = np.array([dq * 0.5, dq * math.sqrt(2.5), dq * math.sqrt(6.5)])
+    b = scatter.bin_intensity(I, n, dx, edges)
+    k = scatter.signed_freq(n)
+    k2 = (k * k)[:, None, None] + (k * k)[None, :, None] + (k * k)[None, None, :]
+    for j, (lo, hi) in enumerate([(1, 2), (3, 6)]):
+        vals = I[(k2 >= lo) & (k2 <= hi)]
+        assert b["count"][j] == vals.size
+        assert math.isclose(b["mean"][j], vals.mean(), rel_tol=1e-13)
+        assert math.isclose(b["sem"][j], vals.std(ddof=1) / math.sqrt(vals.size), rel_tol=1e-10)
+
+
+def _exact_half(x: Fraction) -> Fraction:
+    """Round a rational to the nearest IEEE binary16 value, ties to even (subnormals included)."""
+    if x == 0:
+        return Fraction(0)
+    sgn = -1 if x < 0 else 1
+    a = abs(x)
+    e = math.floor(math.log2(a))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, -14)
+    ulp = Fraction(2) ** (e - 10)
+    q = a / ulp
+    fl = math.floor(q)
+    rem = q - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        fl += 1
+    return sgn * fl * ulp
+
+
+def test_fp16_storage_rounding_is_round_to_nearest_even():
+    """ED stored as FP16 (the ED-1 storage of the three-level workload): float32 -> binary16 RNE."""
+    vals = np.concatenate([RNG.random(200) * 10, RNG.random(50) * 1e-5,
+                           np.array([1 + 2 ** -11, 1 + 3 * 2 ** -11, 2049.0, 2051.0, 6e-8, 3e-8]),
+                           RNG.random(343 - 256) * 1e3]).astype(np.float32)
+    cell = vals.reshape(7, 7, 7)
+    ed = density.tile_mask_density(7, cell, density.ALL, out_dtype="f16")
+    assert ed.dtype == np.float16
+    for x, h in zip(cell.ravel(), ed.ravel()):
+        assert Fraction(float(h)) == _exact_half(Fraction(float(x)))
+
+
+def test_block_sums_exact_for_fp16_and_preserve_electrons():
+    """Sec. 2.3 block integration: FP16 block sums are exact rationals; sum ED-2 = sum ED-1."""
+    ed = (RNG.random((16, 16, 16)) * RNG.choice([1e-3, 1.0, 300.0], size=(16, 16, 16))).astype(np.float16)
+    s = density.block_sums(ed, 4)
+    for (i, j, k) in [(0, 0, 0), (1, 2, 3), (3, 3, 3)]:
+        blk = ed[4 * i:4 * i + 4, 4 * j:4 * j + 4, 4 * k:4 * k + 4]
+        exact = sum(Fraction(float(v)) for v in blk.ravel())
+        assert Fraction(float(s[i, j, k])) == exact
+    assert Fraction(float(s.sum())) == sum(Fraction(float(v)) for v in ed.ravel())
+    z = density.zoom_out(ed, 4, 8, out_dtype="f16")
+    assert z.shape == (8, 8, 8)
+    assert np.all(z[:2] == 0) and np.all(z[6:] == 0)
+    for (i, j, k) in [(0, 0, 0), (3, 1, 2)]:
+        assert Fraction(float(z[2 + i, 2 + j, 2 + k])) == _exact_half(Fraction(float(s[i, j, k])))
+
+
+def test_mask_voxel_counts():
+    """Sec. 2.3 mask: integer-lattice counts of the sphere, cube and octahedron predicates."""
+    n = 24
+    c = (12.0, 12.0, 12.0)
+    rr = 7.0
+    m = density.shape_mask(n, density.SPHERE, c, rr, np.eye(3))
+    cnt = sum(1 for i in range(-12, 12) for j in range(-12, 12) for k in range(-12, 12) if i * i + j * j + k * k <= 49)
+    assert int(m.sum()) == cnt
+    m = density.shape_mask(n, density.CUBE, c, 5.5, np.eye(3))
+    assert int(m.sum()) == 11 ** 3
+    s = 6
+    m = density.shape_mask(n, density.OCTAHEDRON, c, float(s), np.eye(3))
+    assert int(m.sum()) == (2 * s + 1) * (2 * s * s + 2 * s + 3) // 3
+    # rotated solids keep their volume up to the surface voxels
+    rot = inputs.random_rotation(inputs.SplitMix64(3))
+    n = 64
+    c = (32.0, 32.0, 32.0)
+    m = density.shape_mask(n, density.CUBE, c, 12.0, rot)
+    assert abs(m.sum() / 24.0 ** 3 - 1) < 0.03
+    m = density.shape_mask(n, density.OCTAHEDRON, c, 20.0, rot)
+    assert abs(m.sum() / (4.0 / 3.0 * 20.0 ** 3) - 1) < 0.05
+
+
+def test_tile_wrap_and_origin():
+    cell = np.arange(27, dtype=np.float32).reshape(3, 3, 3)
+    t = density.tiled_cell(7, cell, origin=(1, 2, 0))
+    for (z, y, x) in [(0, 0, 0), (6, 5, 4), (3, 1, 2)]:
+        assert t[z, y, x] == cell[z % 3, (y + 2) % 3, (x + 1) % 3]
+
+
+def _loss_from_um(u, m, dx, edges, coeff, origin=(0, 0, 0)):
+    n = m.shape[0]
+    rho = density.tiled_cell(n, u.astype(np.float32), origin).astype(np.float64)
+    # float64 cell values (not the float32 copy) so the finite differences see small steps
+    uu = u[np.ix_((np.arange(n) + origin[2]) % u.shape[0], (np.arange(n) + origin[1]) % u.shape[0],
+                  (np.arange(n) + origin[0]) % u.shape[0])]
+    rho = uu * m
+    b = scatter.forward(rho, dx, edges)
+    mean = np.nan_to_num(b["mean"])
+    return float((coeff * mean ** 2).sum()), b, rho
+
+
+def test_adjoint_matches_finite_differences():
+    """Chain rule of the forward map checked by central differences in FP64."""
+    n, ucell, dx = 8, 4, 0.25
+    u = RNG.random((ucell, ucell, ucell))
+    m = RNG.random((n, n, n))
+    edges = inputs.log_edges(2 * math.pi / (n * dx) * 0.9, math.pi / dx * 1.6, 7)
+    coeff = RNG.random(7) + 0.5
+    L, b, rho = _loss_from_um(u, m, dx, edges, coeff, origin=(1, 0, 2))
+    g = 2 * coeff * np.nan_to_num(b["mean"])
+    grho = adjoint.grad_rho(rho, dx, edges, g, count=b["count"])
+    gu, gm = adjoint.grad_cell_and_mask(grho, u, m, origin=(1, 0, 2))
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 3), (3, 3, 1)]:
+        up, um_ = u.copy(), u.copy()
+        up[idx] += h
+        um_[idx] -= h
+        fd = (_loss_from_um(up, m, dx, edges, coeff, (1, 0, 2))[0] - _loss_from_um(um_, m, dx, edges, coeff, (1, 0, 2))[0]) / (2 * h)
+        assert math.isclose(fd, gu[idx], rel_tol=1e-6, abs_tol=1e-9 * abs(L))
+    for idx in [(0, 0, 0), (4, 5, 6), (7, 1, 3)]:
+        mp, mm = m.copy(), m.copy()
+        mp[idx] += h
+        mm[idx] -= h
+        fd = (_loss_from_um(u, mp, dx, edges, coeff, (1, 0, 2))[0] - _loss_from_um(u, mm, dx, edges, coeff, (1, 0, 2))[0]) / (2 * h)
+        assert math.isclose(fd, gm[idx], rel_tol=1e-6, abs_tol=1e-9 * abs(L))
+
+
+def test_adjoint_directional_derivative():
+    """<dL/drho, d> equals d/dt L(rho + t d) (central difference in t)."""
+    n, dx = 10, 0.1
+    rho = RNG.random((n, n, n))
+    d = RNG.standard_normal((n, n, n))
+    edges = inputs.linear_edges(inputs.nyquist_q(dx), 9)
+    coeff = RNG.random(9)
+
+    def L(r):
+        mean = np.nan_to_num(scatter.forward(r, dx, edges)["mean"])
+        return float((coeff * mean ** 2).sum()), mean
+
+    L0, mean0 = L(rho)
+    grho = adjoint.grad_rho(rho, dx, edges, 2 * coeff * mean0)
+    t = 1e-5
+    fd = (L(rho + t * d)[0] - L(rho - t * d)[0]) / (2 * t)
+    assert math.isclose(fd, float((grho * d).sum()), rel_tol=1e-7)
+
+
+def test_merge_windows_and_absolute_scale():
+    """Sec. 2.5 merge: each output bin comes from the level whose validity window
+    (up to pi/dx) holds its geometric centre, scaled by N^6 to absolute units."""
+    edges = inputs.log_edges(0.05, 20.0, 30)
+    nb = 30
+    lv = []
+    for n, dx, val in [(16, 0.4, 1.0), (16, 0.8, 2.0), (32, 0.1, 3.0)]:
+        lv.append({"n": n, "dx": dx, "count": np.full(nb, 5), "mean": np.full(nb, val),
+                   "sem": np.full(nb, val / 10), "mean_q": np.full(nb, dx)})
+    lv[0]["count"][3] = 0
+    out = merge.merge_levels(lv, edges)
+    qn = {1: math.pi / 0.8, 0: math.pi / 0.4, 2: math.pi / 0.1}
+    for j in range(nb):
+        c = math.sqrt(edges[j] * edges[j + 1])
+        want = 1 if c < qn[1] else (0 if c < qn[0] else (2 if c <= qn[2] else -1))
+        if want == 0 and j == 3:
+            want = -1
+        assert out["source"][j] == want
+        if want >= 0:
+            assert out["mean"][j] == lv[want]["mean"][j] * lv[want]["n"] ** 6
+            assert out["sem"][j] == lv[want]["sem"][j] * lv[want]["n"] ** 6
+        else:
+            assert math.isnan(out["mean"][j]) and out["count"][j] == 0
+
+
+def test_merge_levels_share_forward_scattering():
+    """Block integration keeps the electron count, so N^6 I(0) = N_e^2 at every level
+    (Sec. 2.2 electron-count identity carried through Sec. 2.3 zoom-out)."""
+    n1 = 32
+    shape = inputs.centred_sphere(n1, 10.0)
+    cell = inputs.sc_cell(8, 1.0)
+    ed1 = density.tile_mask_density(n1, cell, density.SPHERE, shape.center, shape.size, out_dtype="f16")
+    ne = float(ed1.astype(np.float64).sum())
+    for f, nout in [(2, 32), (4, 32)]:
+        ed = density.zoom_out(ed1, f, nout, out_dtype="f32")
+        F = scatter.dft3(ed)
+        assert math.isclose(scatter.intensity(F)[0, 0, 0] * nout ** 6, ne ** 2, rel_tol=1e-6)
