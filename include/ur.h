@@ -1,0 +1,237 @@
+/*
+ * ur.h -- C ABI of the GB300 wide-range X-ray scattering hot path.
+ *
+ * The operations follow "Ultima Ratio: simulating wide-range X-ray scattering
+ * and diffraction" (Pauw et al., arXiv 2303.13435):
+ *   ur_build_density  Sec. 2.3: ED-1 = unit cell tiled with periodic wrap and
+ *                     multiplied by the particle mask; ED-2/ED-3 = block
+ *                     integration with zero padding ("zoom out").
+ *   ur_fft_intensity  Sec. 2.4 Eq. 1/Eq. 2: 3D transform split into 2D plane
+ *                     transforms (only planes holding density) and 1D column
+ *                     transforms (absent planes are zeros); I = |F|^2;
+ *                     Sec. 2.5: isotropic averaging of I into Q bins.
+ *   ur_bin_q          Sec. 2.5 averaging of a stored half-spectrum intensity.
+ *   ur_merge          Sec. 2.5 (last paragraph) and Fig. 2: the per-level curves
+ *                     combined into one absolute-scale I(Q).
+ *   ur_backward       Not in the paper: the adjoint of the forward map, from
+ *                     dL/d(bin mean) to dL/d(unit cell) and dL/d(mask weight).
+ *   ur_batch_*        Many particles of uneven grid sizes in one launch sequence.
+ *
+ * Conventions (all calls):
+ *   - Grids are cubic, edge N (even, 8 <= N <= 4096, N/2 a product of 2,3,5,7).
+ *     A density is plane-major rho[z][y][x], x contiguous ("planes" are fixed z).
+ *   - Spectra use the half axis along x: F[kz][ky][kx], kx in [0, N/2],
+ *     complex64 (float2) interleaved, kx contiguous.  Axis index i has the
+ *     signed frequency i (i < N/2) or i - N.  F follows Eq. 1 (1/N^3).
+ *   - |Q| = dq sqrt(k^2), dq = 2 pi / (N dx) (nm^-1), evaluated in IEEE float64;
+ *     bins are half-open [e_j, e_j+1), the last bin closed.
+ *   - Bin statistics are double[UR_BIN_FIELDS][B] (field-major):
+ *       [0] count  voxels of the full N^3 grid in the bin (integer-valued)
+ *       [1] sum of I       [2] sum of I^2      [3] sum of |Q|
+ *       [4] mean I (NaN when count = 0)
+ *       [5] standard error of the mean (NaN when count < 2)
+ *   - Pointers are device pointers unless the argument says "host".  The
+ *     caller owns every buffer; the library owns only ur_plan objects (twiddle
+ *     and bin tables) and allocates nothing else.  Work is queued on `stream`
+ *     (a cudaStream_t; NULL = legacy default stream) and returns before it is
+ *     done unless stated.
+ *   - Every call returns a ur_status; on failure ur_last_error() gives a
+ *     message (per thread).  No call aborts the process.
+ */
+#ifndef UR_H
+#define UR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UR_OK = 0,
+  UR_ERR_INVALID = 1,        /* bad argument: sizes, alignment, null pointer */
+  UR_ERR_OOM = 2,            /* pinned/device allocation inside plan creation failed */
+  UR_ERR_CUDA = 3,           /* a CUDA runtime call failed; message has the CUDA error */
+  UR_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+  UR_ERR_UNSUPPORTED = 5,    /* valid request this build does not implement */
+  UR_ERR_FAULT_INJECTED = 6  /* host-side fault injection (UR_FAULT env) fired */
+} ur_status;
+
+enum { UR_F32 = 0, UR_F16 = 1 };
+
+enum {
+  UR_SHAPE_SPHERE = 0,      /* (dx*dx + dy*dy) + dz*dz <= s*s */
+  UR_SHAPE_CUBE = 1,        /* max_a |p_a| <= s, p = R^T d */
+  UR_SHAPE_OCTAHEDRON = 2,  /* (|p_0| + |p_1|) + |p_2| <= s */
+  UR_SHAPE_ALL = 3,         /* no mask */
+  UR_SHAPE_WEIGHTS = 4      /* per-voxel float32 weights array */
+};
+
+enum { UR_BIN_FIELDS = 6 };
+enum { UR_BIN_COUNT = 0, UR_BIN_SUM_I = 1, UR_BIN_SUM_I2 = 2, UR_BIN_SUM_Q = 3, UR_BIN_MEAN = 4, UR_BIN_SEM = 5 };
+
+/* Last error message of the calling thread ("" if none).  Never NULL. */
+const char* ur_last_error(void);
+const char* ur_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Plans.  A plan fixes the grid, the ED storage type, the slab of planes that
+ * hold density, and the Q bins.  Creation is synchronous: it allocates and
+ * fills the plan's device tables (twiddles exp(-2 pi i t/N) generated in
+ * float64 and rounded to float32; integer k^2 thresholds of the bins; the
+ * data-independent per-bin count and sum of |Q|) on the current device.
+ * ------------------------------------------------------------------------- */
+typedef struct ur_plan ur_plan;
+
+typedef struct {
+  int32_t n;         /* grid edge N */
+  double dx;         /* voxel edge, nm (> 0) */
+  int32_t ed_dtype;  /* UR_F32 or UR_F16: element type of the ED read by ur_fft_intensity */
+  int32_t z0;        /* first plane that may hold density */
+  int32_t nz;        /* number of planes [z0, z0+nz) that may hold density; all others are zero (Sec. 2.4: skipped slices) */
+} ur_grid_desc;
+
+/* edges: host float64[nbins+1], strictly increasing, nm^-1; copied. */
+ur_status ur_plan_create(const ur_grid_desc* grid, const double* edges, int32_t nbins, ur_plan** out);
+ur_status ur_plan_destroy(ur_plan* plan);
+
+/* Bin thresholds: host int64[nbins+1] out; bin j holds k^2 in [t_j, t_j+1). */
+ur_status ur_plan_thresholds(const ur_plan* plan, int64_t* thresholds_out);
+
+/* The same table without a plan (host only, no GPU needed), Sec. 2.5 bin
+ * assignment: t_j = min{s >= 0 : dq sqrt(s) >= e_j} (j < B),
+ * t_B = min{s : dq sqrt(s) > e_B}, dq = 2 pi/(N dx), in IEEE float64.
+ * Values above 3 (N/2)^2 mean "beyond every voxel of the grid". */
+ur_status ur_bin_thresholds(int32_t n, double dx, const double* edges, int32_t nbins, int64_t* thresholds_out);
+
+/* Host-side failure injection (tests): UR_FAULT="<site>:<k>" in the
+ * environment makes the k-th pass through <site> (plan_create,
+ * fft_intensity, backward, host_slab) fail with UR_ERR_FAULT_INJECTED;
+ * ur_fault_reset() re-reads the variable.  Nothing on the device is faulted. */
+void ur_fault_reset(void);
+
+enum { UR_WS_FORWARD = 1, UR_WS_BACKWARD = 2, UR_WS_HOST_SLABS = 4 };
+/* Workspace bytes for the operations in `what` (bitwise OR of UR_WS_*).
+ * The forward workspace holds the plane-transform intermediate
+ * (nz * N * (N/2+1) complex64) and the per-block bin partials; the backward
+ * adds the inverse intermediate (N * N * (N/2+1) complex64).  UR_WS_HOST_SLABS
+ * adds two staging slabs for ED read from pinned host memory. */
+size_t ur_workspace_size(const ur_plan* plan, int32_t what);
+
+/* ---------------------------------------------------------------------------
+ * ur_build_density (Sec. 2.3).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t kind;       /* UR_SHAPE_* */
+  float center[3];    /* (x, y, z) particle centre in voxel-index units */
+  float size;         /* sphere radius, cube half-edge, octahedron vertex distance; voxels */
+  float rot[9];       /* row-major R; body coordinates p = R^T d, d = (x, y, z) - centre */
+} ur_shape;
+
+/* ED-1: rho[z][y][x] = fl32(u[(z+oz)%U][(y+oy)%U][(x+ox)%U] * m(x,y,z)) for
+ * planes z in [z_begin, z_begin+z_count), written plane-major to ed_out
+ * (z_count*N*N elements of out_dtype, FP16 rounded to nearest even).
+ *   cell     device float32[U][U][U]
+ *   origin   host int32[3] (ox, oy, oz), tiling offset, >= 0
+ *   shape    host; kind UR_SHAPE_WEIGHTS reads weights (device float32 N^3,
+ *            full box, plane-major) instead of a predicate.
+ *   nz_range device int32[2] or NULL: atomically lowered/raised to the
+ *            first/last plane written with a nonzero voxel; the caller
+ *            initialises it to {INT32_MAX, -1}.
+ * The mask decision is taken in float32 with separately rounded products and
+ * sums in the order written above (no fused multiply-add). */
+ur_status ur_build_density(int32_t n, const float* cell, int32_t ucell, const int32_t* origin,
+                           const ur_shape* shape, const float* weights, int32_t z_begin,
+                           int32_t z_count, int32_t out_dtype, void* ed_out, int32_t* nz_range,
+                           void* stream);
+
+/* ED-2/ED-3 (Sec. 2.3): out[Z][Y][X] = sum of src over the f^3 block at
+ * (f Z', f Y', f X') where (Z', Y', X') = (Z, Y, X) - o, o = (n_out - n_src/f)/2,
+ * and 0 outside the placed block; out is the full n_out^3 box.  FP16 sources
+ * are summed exactly (integer multiples of 2^-24) and rounded once to the
+ * output type; FP32 sources are summed in float64. */
+ur_status ur_zoom_density(int32_t n_src, int32_t src_dtype, const void* src, int32_t f, int32_t n_out,
+                          int32_t out_dtype, void* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ur_fft_intensity (Sec. 2.4-2.5).
+ *   ed       the nz planes [z0, z0+nz) of the density, plane-major, ed_dtype.
+ *            ed_on_host = 0: device pointer.  ed_on_host = 1: pinned host
+ *            memory; planes are streamed to the device in slabs on an
+ *            internal copy stream, double-buffered, overlapping the plane
+ *            transforms (the workspace must include UR_WS_HOST_SLABS).
+ *   bins     device double[UR_BIN_FIELDS][B] or NULL (no binning).
+ *   F_out    device complex64 [N][N][N/2+1] (Eq. 1 normalised) or NULL.
+ *   ws       device workspace of ur_workspace_size(plan, UR_WS_FORWARD [| UR_WS_HOST_SLABS]).
+ *            The intermediate it holds is what ur_backward recomputes F from.
+ * ------------------------------------------------------------------------- */
+ur_status ur_fft_intensity(const ur_plan* plan, const void* ed, int32_t ed_on_host, double* bins,
+                           void* F_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Sec. 2.5 binning of a stored half-spectrum intensity I[kz][ky][kx]
+ * (device float32, N*N*(N/2+1), Eq. 1 normalised); kx in (0, N/2) weighs 2
+ * (the mirrored half), kx = 0 and N/2 weigh 1.  ws: ur_workspace_size(plan, UR_WS_FORWARD). */
+ur_status ur_bin_q(const ur_plan* plan, const float* intensity_half, double* bins, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ur_merge (Sec. 2.5 last paragraph; Fig. 2 caption).
+ *   nlev        number of levels (1..8)
+ *   level_bins  host array of nlev device pointers, each double[UR_BIN_FIELDS][B]
+ *               binned over the same edges
+ *   level_n     host int32[nlev], grid edge of each level (intensity scale N^6)
+ *   level_qmax  host double[nlev], upper |Q| of each level's validity window
+ *               (pi/dx_level for the Q_max/2 artefact limit with Q_max = 2 pi/dx)
+ *   edges       device double[B+1] (the edges all levels were binned on)
+ *   out         device double[5][B]: mean, sem (absolute units, electrons^2),
+ *               count, mean |Q|, source level (-1: none).
+ * Levels are ordered by level_qmax; the one with the smallest limit covers
+ * [0, its limit), each next one [previous limit, its limit), the last one
+ * closed.  Each output bin takes the level whose window holds sqrt(e_j e_j+1).
+ * ------------------------------------------------------------------------- */
+ur_status ur_merge(int32_t nlev, const double* const* level_bins, const int32_t* level_n,
+                   const double* level_qmax, const double* edges, int32_t nbins, double* out,
+                   void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ur_backward: adjoint of ur_build_density + ur_fft_intensity for a loss L
+ * on the bin means (not in the paper).
+ *   dl_dmean  device double[B], dL/d(mean I_j)
+ *   fwd_bins  device double[UR_BIN_FIELDS][B] from the forward (counts)
+ *   F         device complex64 half spectrum from the forward's F_out, or
+ *             NULL: F is recomputed column by column from the forward
+ *             intermediate still held in ws.
+ *   cell, ucell, origin, shape, weights: as given to ur_build_density.
+ *   dl_dcell  device float32[U][U][U] (overwritten)
+ *   dl_dmask  device float32[N][N][N] (overwritten), or NULL
+ *   ws        the forward's workspace, sized with UR_WS_FORWARD | UR_WS_BACKWARD.
+ * dL/drho(x) = (2/N^3) Re sum_k G_k F_k exp(+2 pi i k.x/N), G_k = dl_dmean_j / count_j
+ * on the voxels of bin j; dL/dm = dL/drho * u(x mod U); dL/du(c) = sum over the
+ * tiles of dL/drho * m.
+ * ------------------------------------------------------------------------- */
+ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double* fwd_bins, const void* F,
+                      const float* cell, int32_t ucell, const int32_t* origin, const ur_shape* shape,
+                      const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,
+                      void* stream);
+
+/* Per-thread event timing of the last ur_fft_intensity on this thread
+ * (milliseconds per internal kernel, in launch order); for measurement only.
+ * Enabled by ur_set_timing(1).  Returns the number of entries written. */
+void ur_set_timing(int32_t enable);
+int32_t ur_last_timings(float* ms_out, int32_t max_entries, const char** names_out);
+
+/* ---------------------------------------------------------------------------
+ * Batched particles (uneven grid sizes).  All plans must share the bin edges'
+ * count B.  eds[i], bins[i] follow ur_fft_intensity for plans[i] (device ED).
+ * ws: ur_batch_workspace_size bytes.  The forward launches one kernel per
+ * pass for the whole batch; ur_batch_backward mirrors ur_backward.
+ * ------------------------------------------------------------------------- */
+size_t ur_batch_workspace_size(int32_t count, const ur_plan* const* plans, int32_t what);
+ur_status ur_batch_forward(int32_t count, const ur_plan* const* plans, const void* const* eds,
+                           double* const* bins, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UR_H */

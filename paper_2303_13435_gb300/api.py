@@ -1,0 +1,292 @@
+"""ctypes binding of libur (include/ur.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory,
+pinned host memory and streams.  Loading fails loudly when libur.so is absent:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libur.so")
+
+UR_F32, UR_F16 = 0, 1
+UR_WS_FORWARD, UR_WS_BACKWARD, UR_WS_HOST_SLABS = 1, 2, 4
+BIN_FIELDS = 6
+BIN_COUNT, BIN_SUM_I, BIN_SUM_I2, BIN_SUM_Q, BIN_MEAN, BIN_SEM = range(6)
+STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID", 2: "UR_ERR_OOM", 3: "UR_ERR_CUDA", 4: "UR_ERR_TIMEOUT",
+          5: "UR_ERR_UNSUPPORTED", 6: "UR_ERR_FAULT_INJECTED"}
+
+# exported symbols of include/ur.h, with (restype, argtypes)
+_vp, _i32, _i64, _sz, _dp = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.POINTER(C.c_double)
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("dx", C.c_double), ("ed_dtype", C.c_int32), ("z0", C.c_int32), ("nz", C.c_int32)]
+
+
+class ShapeDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("center", C.c_float * 3), ("size", C.c_float), ("rot", C.c_float * 9)]
+
+
+SIGNATURES = {
+    "ur_last_error": (C.c_char_p, []),
+    "ur_version": (C.c_char_p, []),
+    "ur_plan_create": (_i32, [C.POINTER(GridDesc), _dp, _i32, C.POINTER(_vp)]),
+    "ur_plan_destroy": (_i32, [_vp]),
+    "ur_plan_thresholds": (_i32, [_vp, C.POINTER(C.c_int64)]),
+    "ur_bin_thresholds": (_i32, [_i32, C.c_double, _dp, _i32, C.POINTER(C.c_int64)]),
+    "ur_fault_reset": (None, []),
+    "ur_workspace_size": (_sz, [_vp, _i32]),
+    "ur_build_density": (_i32, [_i32, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _i32, _i32, _i32,
+                                _vp, _vp, _vp]),
+    "ur_zoom_density": (_i32, [_i32, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "ur_fft_intensity": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "ur_bin_q": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _vp, _vp]),
+    "ur_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
+                           _vp, _sz, _vp]),
+    "ur_set_timing": (None, [_i32]),
+    "ur_last_timings": (_i32, [C.POINTER(C.c_float), _i32, C.POINTER(C.c_char_p)]),
+    "ur_batch_workspace_size": (_sz, [_i32, C.POINTER(_vp), _i32]),
+    "ur_batch_forward": (_i32, [_i32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp, _sz, _vp]),
+}
+# test hooks (not part of the header's API)
+EXTRA = {
+    "ur_selftest_fastdiv": (C.c_int64, []),
+}
+
+_lib = None
+
+
+class UrError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> C.CDLL:
+    """Load libur.so (built by paper_2303_13435_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libur.so not found at {LIB_PATH}: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in {**SIGNATURES, **EXTRA}.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, st: int):
+    if st != 0:
+        raise UrError(fn, st, lib().ur_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dtype_code(d) -> int:
+    if d in ("f32", torch.float32, np.float32):
+        return UR_F32
+    if d in ("f16", torch.float16, np.float16):
+        return UR_F16
+    raise ValueError(f"unsupported ED dtype {d}")
+
+
+def _torch_dtype(code: int):
+    return torch.float32 if code == UR_F32 else torch.float16
+
+
+def shape_desc(shape) -> ShapeDesc:
+    d = ShapeDesc()
+    d.kind = int(shape.kind)
+    c = np.asarray(shape.center, dtype=np.float32)
+    for i in range(3):
+        d.center[i] = float(c[i])
+    d.size = float(np.float32(shape.size))
+    r = np.asarray(shape.rot, dtype=np.float32).reshape(9)
+    for i in range(9):
+        d.rot[i] = float(r[i])
+    return d
+
+
+class Plan:
+    """ur_plan: grid, ED storage type, the nonzero plane slab [z0, z0+nz) and the Q bins."""
+
+    def __init__(self, n: int, dx: float, edges, z0: int = 0, nz: int | None = None, ed_dtype="f32"):
+        self.n = int(n)
+        self.dx = float(dx)
+        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.nbins = len(self.edges) - 1
+        self.z0 = int(z0)
+        self.nz = int(self.n - z0 if nz is None else nz)
+        self.ed_dtype = _dtype_code(ed_dtype)
+        g = GridDesc(self.n, self.dx, self.ed_dtype, self.z0, self.nz)
+        h = C.c_void_p()
+        _check("ur_plan_create", lib().ur_plan_create(C.byref(g), self.edges.ctypes.data_as(_dp), self.nbins, C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def thresholds(self) -> np.ndarray:
+        out = np.zeros(self.nbins + 1, dtype=np.int64)
+        _check("ur_plan_thresholds", lib().ur_plan_thresholds(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def workspace_size(self, what: int = UR_WS_FORWARD) -> int:
+        return int(lib().ur_workspace_size(self._h, what))
+
+    def workspace(self, what: int = UR_WS_FORWARD, device="cuda") -> torch.Tensor:
+        return torch.empty(self.workspace_size(what), dtype=torch.uint8, device=device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ur_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_density(n: int, cell: torch.Tensor, shape, origin=(0, 0, 0), weights: torch.Tensor | None = None,
+                  z_begin: int = 0, z_count: int | None = None, out_dtype="f32", out: torch.Tensor | None = None,
+                  nz_range: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ED-1 planes [z_begin, z_begin + z_count) (Sec. 2.3 tile + mask)."""
+    z_count = n - z_begin if z_count is None else z_count
+    code = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty((z_count, n, n), dtype=_torch_dtype(code), device=cell.device)
+    assert cell.is_cuda and cell.dtype == torch.float32 and cell.is_contiguous()
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
+    sd = shape_desc(shape)
+    _check("ur_build_density", lib().ur_build_density(n, _ptr(cell), cell.shape[0], org, C.byref(sd), _ptr(weights),
+                                                      z_begin, z_count, code, _ptr(out), _ptr(nz_range), _stream(stream)))
+    return out
+
+
+def zoom_density(src: torch.Tensor, f: int, n_out: int, out_dtype="f16", out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """ED-2/ED-3 (Sec. 2.3 block integration + zero padding)."""
+    code = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty((n_out, n_out, n_out), dtype=_torch_dtype(code), device=src.device)
+    _check("ur_zoom_density", lib().ur_zoom_density(src.shape[0], _dtype_code(src.dtype), _ptr(src), f, n_out, code,
+                                                    _ptr(out), _stream(stream)))
+    return out
+
+
+def new_bins(plan: Plan, device="cuda") -> torch.Tensor:
+    return torch.empty((BIN_FIELDS, plan.nbins), dtype=torch.float64, device=device)
+
+
+def fft_intensity(plan: Plan, ed: torch.Tensor, bins: torch.Tensor | None = None, F_out: torch.Tensor | None = None,
+                  ws: torch.Tensor | None = None, stream=None, want_bins: bool = True):
+    """Sec. 2.4-2.5: transform of the nz planes in `ed`, |F|^2 and Q-bin statistics.
+
+    `ed` holds planes [z0, z0+nz) (device, or pinned host for the streamed path).
+    Returns the bins tensor [6, B] (count, sum I, sum I^2, sum |Q|, mean, sem)."""
+    on_host = 0 if ed.is_cuda else 1
+    what = UR_WS_FORWARD | (UR_WS_HOST_SLABS if on_host else 0)
+    if ws is None:
+        ws = plan.workspace(what)
+    if bins is None and want_bins:
+        bins = new_bins(plan)
+    _check("ur_fft_intensity", lib().ur_fft_intensity(plan.handle, _ptr(ed), on_host, _ptr(bins), _ptr(F_out), _ptr(ws),
+                                                      ws.numel(), _stream(stream)))
+    return bins
+
+
+def bin_q(plan: Plan, I_half: torch.Tensor, bins: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if bins is None:
+        bins = new_bins(plan)
+    _check("ur_bin_q", lib().ur_bin_q(plan.handle, _ptr(I_half), _ptr(bins), None, 0, _stream(stream)))
+    return bins
+
+
+def merge(level_bins: list, level_n: list, level_qmax: list, edges_dev: torch.Tensor, out: torch.Tensor | None = None,
+          stream=None) -> torch.Tensor:
+    """Sec. 2.5 merge of level curves into absolute units; out[5, B] = mean, sem, count, mean Q, source."""
+    nlev = len(level_bins)
+    nb = edges_dev.numel() - 1
+    if out is None:
+        out = torch.empty((5, nb), dtype=torch.float64, device=edges_dev.device)
+    ptrs = (C.c_void_p * nlev)(*[b.data_ptr() for b in level_bins])
+    ns = (C.c_int32 * nlev)(*[int(v) for v in level_n])
+    qs = (C.c_double * nlev)(*[float(v) for v in level_qmax])
+    _check("ur_merge", lib().ur_merge(nlev, ptrs, ns, qs, _ptr(edges_dev), nb, _ptr(out), _stream(stream)))
+    return out
+
+
+def backward(plan: Plan, dl_dmean: torch.Tensor, fwd_bins: torch.Tensor, cell: torch.Tensor, shape, ws: torch.Tensor,
+             origin=(0, 0, 0), weights: torch.Tensor | None = None, F: torch.Tensor | None = None,
+             dl_dcell: torch.Tensor | None = None, dl_dmask: torch.Tensor | None = None, want_mask: bool = True,
+             stream=None):
+    """Adjoint: dL/d(mean I) -> (dL/d cell, dL/d mask).  `ws` is the forward's workspace
+    (sized UR_WS_FORWARD | UR_WS_BACKWARD) still holding the forward intermediate."""
+    n = plan.n
+    if dl_dcell is None:
+        dl_dcell = torch.empty_like(cell)
+    if dl_dmask is None and want_mask:
+        dl_dmask = torch.empty((n, n, n), dtype=torch.float32, device=cell.device)
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
+    sd = shape_desc(shape)
+    _check("ur_backward", lib().ur_backward(plan.handle, _ptr(dl_dmean), _ptr(fwd_bins), _ptr(F), _ptr(cell),
+                                            cell.shape[0], org, C.byref(sd), _ptr(weights), _ptr(dl_dcell),
+                                            _ptr(dl_dmask), _ptr(ws), ws.numel(), _stream(stream)))
+    return dl_dcell, dl_dmask
+
+
+def bin_thresholds(n: int, dx: float, edges) -> np.ndarray:
+    """Integer k^2 thresholds of the bins (host computation, no GPU)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.zeros(len(e), dtype=np.int64)
+    _check("ur_bin_thresholds", lib().ur_bin_thresholds(n, dx, e.ctypes.data_as(_dp), len(e) - 1,
+                                                        out.ctypes.data_as(C.POINTER(C.c_int64))))
+    return out
+
+
+def set_timing(enable: bool):
+    lib().ur_set_timing(1 if enable else 0)
+
+
+def last_timings(max_entries: int = 4096):
+    ms = (C.c_float * max_entries)()
+    names = (C.c_char_p * max_entries)()
+    n = lib().ur_last_timings(ms, max_entries, names)
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/ur.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "ur.h")
+    txt = open(hdr).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ur_[a-z0-9_]+)\s*\(", txt)))
+
+
+def qmax_nyquist(dx: float) -> float:
+    return math.pi / dx

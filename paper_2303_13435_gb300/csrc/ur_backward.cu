@@ -1,0 +1,252 @@
+// Adjoint of the forward map (not in the paper; the chain rule through
+// Sec. 2.3-2.5).  For g_j = dL/d(mean I_j) and G_k = g_j / n_j on bin j:
+//
+//   dL/drho(x) = (2/N^3) Re sum_k G_k F_k e^{+2 pi i k.x/N}
+//              = (1/N^3) Re sum_k sigma_j F~_k e^{+2 pi i k.x/N},  sigma_j = 2 g_j / (n_j N^3)
+//
+// with F~ the unnormalised transform.  The inverse transform runs in the
+// reverse order of the forward passes:
+//   B1 k_cols<COL_ZADJ>  per (ky, kx) column: F~ along z recomputed from the
+//                        forward intermediate (or F read), times sigma(bin),
+//                        inverse transform along z, all N planes written
+//   B2 k_cols<COL_Y,inv> inverse transform along y of every plane, in place
+//   B3 k_rows_grad       inverse real transform along x of every row, then
+//                        dL/dm = dL/drho * u(x mod U) written and
+//                        dL/du(c) = sum over tiles of dL/drho * m(x) reduced;
+//                        a block takes a batch of the grid rows that wrap
+//                        onto one cell row (cz, cy), so its partial sums of
+//                        dL/du land on one cell row (one global add each).
+#include <math.h>
+#include <string.h>
+
+#include "ur_forward.cuh"
+
+struct GradShape {
+  int kind;
+  float cx, cy, cz, s;
+  float r[9];
+};
+
+__device__ __forceinline__ float grad_mask_at(const GradShape& sh, int x, int y, int z) {
+  if (sh.kind == UR_SHAPE_ALL) return 1.f;
+  const float dx = __fsub_rn((float)x, sh.cx);
+  const float dy = __fsub_rn((float)y, sh.cy);
+  const float dz = __fsub_rn((float)z, sh.cz);
+  if (sh.kind == UR_SHAPE_SPHERE) {
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return d2 <= __fmul_rn(sh.s, sh.s) ? 1.f : 0.f;
+  }
+  float p[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    p[a] = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(sh.r[a], dx), __fmul_rn(sh.r[3 + a], dy)), __fmul_rn(sh.r[6 + a], dz)));
+  if (sh.kind == UR_SHAPE_CUBE) return (p[0] <= sh.s && p[1] <= sh.s && p[2] <= sh.s) ? 1.f : 0.f;
+  return __fadd_rn(__fadd_rn(p[0], p[1]), p[2]) <= sh.s ? 1.f : 0.f;
+}
+
+// sigma_j = 2 g_j / (n_j N^3) (scale of F~), or 2 g_j / n_j when F (= F~/N^3) is read
+__global__ void k_sigma(const double* __restrict__ g, const double* __restrict__ fwd_bins, int nb, double n3, int f_given,
+                        float* __restrict__ sigma) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double n = fwd_bins[UR_BIN_COUNT * nb + j];
+  double v = 0.0;
+  if (n > 0) v = 2.0 * g[j] / n / (f_given ? 1.0 : n3);
+  sigma[j] = (float)v;
+}
+
+// B3.  Block (cz, cy); rows (z, y) with (z+oz) mod U = cz and (y+oy) mod U = cy.
+// Each row: Y[z][y][0..M] (Hermitian half along x) -> Z[k] = E[k] + i O[k],
+//   E[k] = X[k] + conj X[M-k],  O[k] = (X[k] - conj X[M-k]) conj(W_N^k),
+// then z = IFFT_{M}(Z) gives (g(2m), g(2m+1)) = (Re z[m], Im z[m]).
+__global__ void __launch_bounds__(256, 2) k_rows_grad(const float2* __restrict__ Y, int N, int RB,
+                                                   const StageInfo* __restrict__ sched, int nst,
+                                                   const float2* __restrict__ tw, const float* __restrict__ cell, int U,
+                                                   int ox, int oy, int oz, GradShape sh, const float* __restrict__ weights,
+                                                   float inv_n3, float* __restrict__ dl_dmask, float* __restrict__ dl_dcell) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int M = N >> 1, H = M + 1;
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float* acc = reinterpret_cast<float*>(smraw + ur_align_up_dev((size_t)RB * H * sizeof(float2), 16));
+  const int cz = blockIdx.y / U, cy = blockIdx.y - (blockIdx.y / U) * U;
+  const int zf = ((cz - oz) % U + U) % U, yf = ((cy - oy) % U + U) % U;
+  const int nzr = zf < N ? (N - 1 - zf) / U + 1 : 0;
+  const int nyr = yf < N ? (N - 1 - yf) / U + 1 : 0;
+  const int nrows = nzr * nyr;
+  const int r0 = blockIdx.x * RB;
+  if (r0 >= nrows) return;  // uniform over the block
+  for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
+  const float* crow = cell + ((long long)cz * U + cy) * U;
+  const FastDiv dM((uint32_t)M), dH((uint32_t)H), dNy((uint32_t)(nyr > 0 ? nyr : 1));
+  __syncthreads();
+  {
+    const int nb = min(RB, nrows - r0);
+    // load rows
+    for (int f = threadIdx.x; f < RB * H; f += blockDim.x) {
+      const int t = (int)dH.div((uint32_t)f);
+      const int k = f - t * H;
+      float2 v = make_float2(0.f, 0.f);
+      if (t < nb) {
+        const int q = r0 + t;
+        const int a = (int)dNy.div((uint32_t)q);
+        const int b = q - a * nyr;
+        const long long z = zf + (long long)U * a, y = yf + (long long)U * b;
+        v = __ldg(Y + (z * N + y) * H + k);
+      }
+      buf[f] = v;
+    }
+    __syncthreads();
+    // Hermitian half -> packed complex sequence, in place by (k, M-k) pairs
+    const int half = M / 2 + 1;
+    for (int f = threadIdx.x; f < RB * half; f += blockDim.x) {
+      const int t = f / half;
+      const int k = f - t * half;
+      float2* X = buf + t * H;
+      const float2 xa = X[k], xb = X[M - k];
+      const float2 wa = __ldg(tw + k);
+      // Z[k]
+      const float2 ea = cadd(xa, cconj(xb));
+      const float2 da = csub(xa, cconj(xb));
+      const float2 oa = make_float2(da.x * wa.x + da.y * wa.y, da.y * wa.x - da.x * wa.y);  // * conj(W^k)
+      const float2 za = make_float2(ea.x - oa.y, ea.y + oa.x);
+      if (k != 0 && 2 * k != M) {
+        const float2 wb = __ldg(tw + (M - k));
+        const float2 eb = cadd(xb, cconj(xa));
+        const float2 db = csub(xb, cconj(xa));
+        const float2 ob = make_float2(db.x * wb.x + db.y * wb.y, db.y * wb.x - db.x * wb.y);
+        X[M - k] = make_float2(eb.x - ob.y, eb.y + ob.x);
+      }
+      X[k] = za;
+    }
+    __syncthreads();
+    fft_lines<true, UR_EMAX>(buf, H, RB, sched, nst, tw);
+    // epilogue
+    for (int f = threadIdx.x; f < RB * M; f += blockDim.x) {
+      const int t = (int)dM.div((uint32_t)f);
+      const int m = f - t * M;
+      if (t >= nb) continue;
+      const int q = r0 + t;
+      const int a = (int)dNy.div((uint32_t)q);
+      const int b = q - a * nyr;
+      const int z = zf + U * a, y = yf + U * b;
+      const float2 zv = buf[t * H + m];
+      const float g0 = zv.x * inv_n3, g1 = zv.y * inv_n3;
+      const int x0 = 2 * m;
+      const int c0 = (x0 + ox) % U, c1 = (x0 + 1 + ox) % U;
+      const long long vox = ((long long)z * N + y) * N + x0;
+      if (dl_dmask) {
+        const float u0 = __ldg(crow + c0), u1 = __ldg(crow + c1);
+        *reinterpret_cast<float2*>(dl_dmask + vox) = make_float2(g0 * u0, g1 * u1);
+      }
+      float m0, m1;
+      if (sh.kind == UR_SHAPE_WEIGHTS) {
+        const float2 wv = __ldg(reinterpret_cast<const float2*>(weights + vox));
+        m0 = wv.x;
+        m1 = wv.y;
+      } else {
+        m0 = grad_mask_at(sh, x0, y, z);
+        m1 = grad_mask_at(sh, x0 + 1, y, z);
+      }
+      if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
+      if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < U; i += blockDim.x)
+    if (acc[i] != 0.f) atomicAdd(dl_dcell + ((long long)cz * U + cy) * U + i, acc[i]);
+}
+
+extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const double* fwd_bins, const void* F,
+                                 const float* cell, int32_t ucell, const int32_t* origin, const ur_shape* shape,
+                                 const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  UR_REQUIRE(p && dl_dmean && fwd_bins && cell && shape && dl_dcell && ws, "ur_backward: null argument");
+  UR_REQUIRE(ucell >= 1, "ur_backward: empty cell");
+  UR_REQUIRE(ws_bytes >= ur_workspace_size(p, UR_WS_FORWARD | UR_WS_BACKWARD), "ur_backward: workspace %zu < %zu bytes",
+             ws_bytes, ur_workspace_size(p, UR_WS_FORWARD | UR_WS_BACKWARD));
+  UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_backward: bad shape kind");
+  UR_REQUIRE(shape->kind != UR_SHAPE_WEIGHTS || weights, "ur_backward: weights required for UR_SHAPE_WEIGHTS");
+  UR_REQUIRE(!dl_dmask || ((uintptr_t)dl_dmask % 8) == 0, "ur_backward: dl_dmask must be 8-byte aligned");
+  UR_TRY(ur_fault_point("backward"));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = p->n, H = p->H, nb = p->nbins;
+  const double n3 = (double)n * n * n;
+  float2* X = (float2*)ws;
+  float2* Y = (float2*)((char*)ws + ur_align_up(p->ws_inter, 256));
+  float* sigma = (float*)((char*)Y + ur_align_up(p->ws_inv, 256));
+
+  ur_timing_begin("sigma", s);
+  k_sigma<<<(nb + 255) / 256, 256, 0, s>>>(dl_dmean, fwd_bins, nb, n3, F != nullptr, sigma);
+  UR_LAUNCH_CHECK("k_sigma");
+  ur_timing_end(s);
+
+  // B1
+  ColArgs a = ur_col_args(p);
+  a.ncols = (long long)n * H;
+  a.A = H;
+  a.S = (long long)n * H;
+  a.Ad = H;
+  a.Sd = (long long)n * H;
+  a.dst = Y;
+  a.sigma = sigma;
+  if (F) {
+    a.src = (const float2*)F;
+    a.nload = n;
+    a.zoff = 0;
+    a.skip_fwd = 1;
+  } else {
+    a.src = X;
+    a.nload = p->nz;
+    a.zoff = p->z0;
+    a.skip_fwd = 0;
+  }
+  const long long tiles = (a.ncols + a.TX - 1) / a.TX;
+  ur_timing_begin("adj_cols_z", s);
+  UR_TRY(ur_launch_cols(COL_ZADJ, false, p, a, (int)tiles, p->col_smem, s));
+  ur_timing_end(s);
+
+  // B2
+  ColArgs b = ur_col_args(p);
+  b.src = Y;
+  b.dst = Y;
+  b.ncols = (long long)n * H;
+  b.A = (long long)n * H;
+  b.S = H;
+  b.Ad = b.A;
+  b.Sd = b.S;
+  b.nload = n;
+  b.zoff = 0;
+  b.nbins = 0;
+  ur_timing_begin("adj_cols_y", s);
+  UR_TRY(ur_launch_cols(COL_Y, true, p, b, (int)tiles, p->col_smem, s));
+  ur_timing_end(s);
+
+  // B3
+  GradShape sh;
+  sh.kind = shape->kind;
+  sh.cx = shape->center[0];
+  sh.cy = shape->center[1];
+  sh.cz = shape->center[2];
+  sh.s = shape->size;
+  memcpy(sh.r, shape->rot, sizeof sh.r);
+  int ox = 0, oy = 0, oz = 0;
+  if (origin) {
+    ox = origin[0];
+    oy = origin[1];
+    oz = origin[2];
+  }
+  const int RB = p->row_rb;
+  const size_t smem = ur_align_up((size_t)RB * H * sizeof(float2), 16) + (size_t)ucell * sizeof(float);
+  UR_REQUIRE(smem <= 227 * 1024, "ur_backward: cell edge %d too large for the row reduction", ucell);
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  UR_REQUIRE((long long)ucell * ucell <= 65535, "ur_backward: cell edge %d too large", ucell);
+  const int rows_per_group = ((n + ucell - 1) / ucell) * ((n + ucell - 1) / ucell);
+  dim3 ggrid((unsigned)((rows_per_group + RB - 1) / RB), (unsigned)(ucell * ucell));
+  UR_CUDA_CHECK(cudaMemsetAsync(dl_dcell, 0, sizeof(float) * (size_t)ucell * ucell * ucell, s));
+  ur_timing_begin("adj_rows_grad", s);
+  k_rows_grad<<<ggrid, 256, smem, s>>>(Y, n, RB, p->d_sched + UR_MAX_STAGES, p->sched_m.nst, p->tw, cell, ucell,
+                                               ox, oy, oz, sh, weights, (float)(1.0 / n3), dl_dmask, dl_dcell);
+  UR_LAUNCH_CHECK("k_rows_grad");
+  ur_timing_end(s);
+  return UR_OK;
+}

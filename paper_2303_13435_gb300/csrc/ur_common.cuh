@@ -1,0 +1,393 @@
+// Internal definitions shared by the CUDA translation units of libur.
+//
+// Complex arithmetic, the small DFT butterflies, the shared-memory Stockham
+// FFT engine, integer bin lookup, and the plan structure.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "ur.h"
+
+// ---------------------------------------------------------------------------
+// Host error reporting
+// ---------------------------------------------------------------------------
+void ur_set_error(const char* fmt, ...);
+ur_status ur_fault_point(const char* site);  // host-side fault injection (UR_FAULT=<site>:<n>)
+
+#define UR_CUDA_CHECK(call)                                                                  \
+  do {                                                                                       \
+    cudaError_t ur_e_ = (call);                                                              \
+    if (ur_e_ != cudaSuccess) {                                                              \
+      ur_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(ur_e_), __FILE__, __LINE__); \
+      return UR_ERR_CUDA;                                                                    \
+    }                                                                                        \
+  } while (0)
+
+#define UR_LAUNCH_CHECK(name)                                                                \
+  do {                                                                                       \
+    cudaError_t ur_e_ = cudaGetLastError();                                                  \
+    if (ur_e_ != cudaSuccess) {                                                              \
+      ur_set_error("launch of %s failed: %s", name, cudaGetErrorString(ur_e_));             \
+      return UR_ERR_CUDA;                                                                    \
+    }                                                                                        \
+  } while (0)
+
+#define UR_REQUIRE(cond, ...)                                                                \
+  do {                                                                                       \
+    if (!(cond)) {                                                                           \
+      ur_set_error(__VA_ARGS__);                                                             \
+      return UR_ERR_INVALID;                                                                 \
+    }                                                                                        \
+  } while (0)
+
+#define UR_TRY(expr)                      \
+  do {                                    \
+    ur_status ur_s_ = (expr);             \
+    if (ur_s_ != UR_OK) return ur_s_;     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Division by a run-time constant: q = (umulhi(x, m) + x) >> s with
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1 (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994).
+// Exact for 0 <= x < 2^31 and 1 <= d < 2^31.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  uint32_t d, m, s;
+  __host__ __device__ FastDiv() : d(1), m(1), s(0) {}
+  __host__ __device__ explicit FastDiv(uint32_t dd) : d(dd) {
+    uint32_t sh = 0;
+    while ((1ull << sh) < dd) ++sh;
+    s = sh;
+    m = (uint32_t)(((1ull << 32) * ((1ull << sh) - dd)) / dd + 1);
+  }
+  __host__ __device__ __forceinline__ uint32_t div(uint32_t x) const {
+#ifdef __CUDA_ARCH__
+    uint32_t hi = __umulhi(x, m);
+#else
+    uint32_t hi = (uint32_t)(((uint64_t)x * m) >> 32);
+#endif
+    return (hi + x) >> s;
+  }
+  __host__ __device__ __forceinline__ uint32_t mod(uint32_t x) const { return x - div(x) * d; }
+};
+
+// ---------------------------------------------------------------------------
+// Complex helpers (float2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * (-i) for the forward direction, a * (+i) for the inverse
+template <bool INV>
+__device__ __forceinline__ float2 mul_ni(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// Twiddle load through the read-only path.  The asm is volatile so that the
+// compiler does not hoist the (loop-invariant) loads of every stage out of a
+// kernel's outer loop and keep them all in registers.
+__device__ __forceinline__ float2 ld_twiddle(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+// a * W where W is the forward twiddle (inverse: conj(W))
+template <bool INV>
+__device__ __forceinline__ float2 twmul(float2 a, float2 w) {
+  return INV ? make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers.  Forward: y_p = sum_m a_m exp(-2 pi i m p / R);
+// inverse: the conjugate kernel (no scaling).
+// ---------------------------------------------------------------------------
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+  float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  float2 t2 = cadd(a1, a3), t3 = mul_ni<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* a) {
+  // even/odd split into two 4-point DFTs, then W8^k combination
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const float r = 0.70710678118654752f;
+  // o1 *= W8^1, o2 *= W8^2, o3 *= W8^3
+  if (!INV) {
+    o1 = make_float2((o1.x + o1.y) * r, (o1.y - o1.x) * r);
+    o2 = make_float2(o2.y, -o2.x);
+    o3 = make_float2((o3.y - o3.x) * r, -(o3.x + o3.y) * r);
+  } else {
+    o1 = make_float2((o1.x - o1.y) * r, (o1.x + o1.y) * r);
+    o2 = make_float2(-o2.y, o2.x);
+    o3 = make_float2(-(o3.x + o3.y) * r, (o3.x - o3.y) * r);
+  }
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+// Odd prime R in {3, 5, 7}: pair a_m with a_{R-m}; y_p = t_p -/+ i u_p.
+template <int R>
+struct OddConst;
+template <>
+struct OddConst<3> {
+  __device__ static constexpr float c(int q) { return -0.5f; }
+  __device__ static constexpr float s(int q) { return q == 1 ? 0.86602540378443865f : -0.86602540378443865f; }
+};
+template <>
+struct OddConst<5> {
+  __device__ static constexpr float c(int q) {
+    return (q == 1 || q == 4) ? 0.30901699437494742f : -0.80901699437494742f;
+  }
+  __device__ static constexpr float s(int q) {
+    return q == 1 ? 0.95105651629515357f : q == 2 ? 0.58778525229247313f : q == 3 ? -0.58778525229247313f
+                                                                                  : -0.95105651629515357f;
+  }
+};
+template <>
+struct OddConst<7> {
+  __device__ static constexpr float c(int q) {
+    return (q == 1 || q == 6) ? 0.62348980185873353f : (q == 2 || q == 5) ? -0.22252093395631440f
+                                                                           : -0.90096886790241913f;
+  }
+  __device__ static constexpr float s(int q) {
+    return q == 1 ? 0.78183148246802981f : q == 2 ? 0.97492791218182361f : q == 3 ? 0.43388373911755812f
+           : q == 4 ? -0.43388373911755812f : q == 5 ? -0.97492791218182361f : -0.78183148246802981f;
+  }
+};
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_odd(float2* a) {
+  constexpr int h = (R - 1) / 2;
+  float2 b[h], d[h];
+#pragma unroll
+  for (int m = 1; m <= h; ++m) {
+    b[m - 1] = cadd(a[m], a[R - m]);
+    d[m - 1] = csub(a[m], a[R - m]);
+  }
+  float2 y0 = a[0];
+#pragma unroll
+  for (int m = 0; m < h; ++m) y0 = cadd(y0, b[m]);
+  float2 y[R];
+  y[0] = y0;
+#pragma unroll
+  for (int p = 1; p <= h; ++p) {
+    float2 t = a[0];
+    float2 u = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m <= h; ++m) {
+      const int q = (m * p) % R;
+      const float cc = OddConst<R>::c(q), ss = OddConst<R>::s(q);
+      t.x = fmaf(cc, b[m - 1].x, t.x);
+      t.y = fmaf(cc, b[m - 1].y, t.y);
+      u.x = fmaf(ss, d[m - 1].x, u.x);
+      u.y = fmaf(ss, d[m - 1].y, u.y);
+    }
+    // forward: y_p = t - i u, y_{R-p} = t + i u
+    float2 iu = make_float2(-u.y, u.x);
+    if (!INV) {
+      y[p] = csub(t, iu);
+      y[R - p] = cadd(t, iu);
+    } else {
+      y[p] = cadd(t, iu);
+      y[R - p] = csub(t, iu);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < R; ++p) a[p] = y[p];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* a) {
+  if constexpr (R == 2) {
+    dft2<INV>(a[0], a[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(a[0], a[1], a[2], a[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(a);
+  } else {
+    dft_odd<R, INV>(a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Radix schedule of a length-L FFT that reads its twiddles from a table of
+// length n_tab (exp(-2 pi i t / n_tab), generated in float64 on the host).
+// Stage st has radix R, butterflies per line nb = L/R, and Ns = product of the
+// radices of the earlier stages.
+// ---------------------------------------------------------------------------
+#define UR_MAX_STAGES 14
+struct StageInfo {
+  int R, nb, Ns, tstep;  // tstep = n_tab / (Ns * R)
+  FastDiv div_nb, div_ns;
+};
+struct Sched {
+  int L, nst;
+  StageInfo st[UR_MAX_STAGES];
+};
+
+bool ur_make_sched(int L, int n_tab, Sched* out);  // host; false if L is not {2,3,5,7}-smooth
+
+// One Stockham autosort stage, in place in shared memory (pitch between
+// lines), all threads of the block participating.  Each thread first loads
+// every input of its butterflies into registers, the block synchronises, and
+// then it writes the outputs, so reads and writes of the stage never race.
+//   input  of butterfly j (line l): x[l][j + r nb], r = 0..R-1
+//   twiddle exp(-2 pi i r k / (Ns R)), k = j mod Ns
+//   output y[l][(j - k) R + k + r Ns]
+template <int R, bool INV, int EMAX>
+__device__ __forceinline__ void fft_stage(float2* __restrict__ buf, int pitch, int lines, const StageInfo& si,
+                                          const float2* __restrict__ tw) {
+  constexpr int BMAX = (EMAX + R - 1) / R;
+  const int nb = si.nb;
+  const int total = lines * nb;
+  float2 v[BMAX][R];
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    const int w = threadIdx.x + b * blockDim.x;
+    if (w < total) {
+      const int line = (int)si.div_nb.div((uint32_t)w);
+      const int j = w - line * nb;
+      const float2* src = buf + line * pitch + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = src[r * nb];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    const int w = threadIdx.x + b * blockDim.x;
+    if (w < total) {
+      const int line = (int)si.div_nb.div((uint32_t)w);
+      const int j = w - line * nb;
+      const int k = (int)si.div_ns.mod((uint32_t)j);
+      if (si.Ns > 1 && k > 0) {
+        const int step = k * si.tstep;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = twmul<INV>(v[b][r], ld_twiddle(tw + r * step));
+      }
+      dft<R, INV>(v[b]);
+      float2* dst = buf + line * pitch + (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * si.Ns] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// FFT of `lines` lines held in shared memory (pitch apart), in place, with the
+// stage table `st` (nst stages, device memory).  Requires lines * L <= EMAX *
+// blockDim.x.  Every thread of the block must call it.
+// The stages of one radix run in their own loop (schedules list radices in
+// the order 8, 4, 2, 3, 5, 7): a single loop with a switch over the radix
+// makes the compiler keep the register arrays of every case live at once.
+template <int R, bool INV, int EMAX>
+__device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, const StageInfo* __restrict__ st,
+                                             int nst, const float2* __restrict__ tw, int i) {
+  while (i < nst) {
+    StageInfo si;
+    {
+      // volatile: keep the per-stage loads inside the caller's loops
+      const volatile StageInfo* vs = st + i;
+      si.R = vs->R;
+      si.nb = vs->nb;
+      si.Ns = vs->Ns;
+      si.tstep = vs->tstep;
+      si.div_nb.d = vs->div_nb.d;
+      si.div_nb.m = vs->div_nb.m;
+      si.div_nb.s = vs->div_nb.s;
+      si.div_ns.d = vs->div_ns.d;
+      si.div_ns.m = vs->div_ns.m;
+      si.div_ns.s = vs->div_ns.s;
+    }
+    if (si.R != R) break;
+    fft_stage<R, INV, EMAX>(buf, pitch, lines, si, tw);
+    ++i;
+  }
+  return i;
+}
+
+template <bool INV, int EMAX>
+__device__ __forceinline__ void fft_lines(float2* buf, int pitch, int lines, const StageInfo* __restrict__ st, int nst,
+                          const float2* __restrict__ tw) {
+  int i = 0;
+  i = fft_stages_of<8, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<4, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<2, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+}
+
+// ---------------------------------------------------------------------------
+// Bin lookup on integer k^2: bin j holds s in [t_j, t_j+1); -1 / B outside.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bin_search(const int32_t* __restrict__ thr, int nb, int s) {
+  // largest j in [0, nb] with thr[j] <= s, or -1
+  int lo = 0, hi = nb + 1;  // answer + 1 in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (thr[mid] <= s) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct ur_plan {
+  int n, M, H;       // grid edge, N/2, N/2+1
+  double dx, dq;
+  int ed_dtype, z0, nz, nbins;
+  int device, num_sms;
+  float2* tw;        // device [n]
+  int32_t* thr;      // device [nbins+1]
+  int64_t* thr_host; // host   [nbins+1]
+  double* geo;       // device [2][nbins]: count, sum |Q|
+  Sched sched_n, sched_m;       // host copies
+  StageInfo* d_sched;           // device: [0, UR_MAX_STAGES) length N, then length N/2
+  // launch configuration
+  int row_threads, row_rb;        // forward/inverse row kernels: rows per block
+  int col_threads, col_tx;        // column kernels: columns per block
+  int zbin_grid;                  // persistent blocks of the binned column pass
+  size_t row_smem, col_smem, colbin_smem;
+  // workspace layout (bytes)
+  size_t ws_inter;   // nz * N * H complex64
+  size_t ws_inv;     // N * N * H complex64
+  size_t ws_sigma;   // nbins floats (+pad)
+  size_t ws_slab;    // one host-staging slab
+  int slab_planes;
+};
+
+// kernels launched from host code in other translation units
+ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s);
+
+static inline size_t ur_align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -1,0 +1,603 @@
+// Forward path: Sec. 2.4 separated transform (Eq. 2) and Sec. 2.5 Q binning.
+//
+//   pass 1a  k_rows_r2c        real-to-complex transform along x of every row of
+//                              the planes that hold density (two reals packed as
+//                              one complex, N/2-point FFT, then the split step)
+//   pass 1b  k_cols<COL_Y>     complex transform along y of each (plane, kx)
+//                              column, in place: with 1a, the 2D transform of
+//                              every nonzero plane (inner sum of Eq. 2)
+//   pass 2   k_cols<COL_ZBIN>  complex transform along z of each (ky, kx)
+//                              column; planes outside [z0, z0+nz) enter as zeros
+//                              (Sec. 2.4: skipped slices are padded); |F|^2 and
+//                              the Q-bin sums are taken from shared memory
+//   k_finalize                 per-bin counts, sums, mean and standard error
+//
+// Layouts: intermediate X[p][y][kx] (p = plane - z0), complex64, kx contiguous,
+// N/2+1 per row.  Columns of pass 1b are c = p*(N/2+1) + kx; columns of pass 2
+// are c = ky_index*(N/2+1) + kx.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "ur_forward.cuh"
+
+#define BIN_CHUNK 8  // consecutive |kz| per thread in the binning walk
+
+// ---------------------------------------------------------------------------
+// Pass 1a
+// Row r (r = p*N + y) holds N reals read as N/2 complex z[m] = (x[2m], x[2m+1]);
+// Z = FFT_{N/2}(z); then, with Z[M] = Z[0],
+//   X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2,  k = 0..M,
+// which recombines the transforms of the even and the odd samples.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float2 load_pair(const T* p);
+template <>
+__device__ __forceinline__ float2 load_pair<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+template <>
+__device__ __forceinline__ float2 load_pair<__half>(const __half* p) {
+  __half2 h = __ldg(reinterpret_cast<const __half2*>(p));
+  return __half22float2(h);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_rows_r2c(const T* __restrict__ ed, float2* __restrict__ X, long long nrows,
+                                                  int N, int RB, const StageInfo* __restrict__ sched, int nst,
+                                                  const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  const int M = N >> 1, H = M + 1;
+  const long long r0 = (long long)blockIdx.x * RB;
+  const FastDiv dm((uint32_t)M), dh((uint32_t)H);
+  for (int f = threadIdx.x; f < RB * M; f += blockDim.x) {
+    const int t = (int)dm.div((uint32_t)f);
+    const int m = f - t * M;
+    const long long r = r0 + t;
+    smem[f] = (r < nrows) ? load_pair<T>(ed + r * N + 2 * m) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_lines<false, UR_EMAX>(smem, M, RB, sched, nst, tw);
+  for (int f = threadIdx.x; f < RB * H; f += blockDim.x) {
+    const int t = (int)dh.div((uint32_t)f);
+    const int k = f - t * H;
+    const long long r = r0 + t;
+    if (r >= nrows) continue;
+    const float2* Z = smem + t * M;
+    const float2 zk = Z[k == M ? 0 : k];
+    const float2 zc = cconj(Z[k == 0 ? 0 : M - k]);
+    const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+    const float2 d = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
+    const float2 o = make_float2(d.y, -d.x);  // -i d
+    const float2 w = __ldg(tw + k);
+    X[r * H + k] = cadd(e, cmul(w, o));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column passes.  A block owns TX consecutive columns; column c of the source
+// has elements src[(c / H) * A + c % H + i * S], i < nload, placed at shared
+// position zoff + i (all other positions zero).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long col_offset(long long c, int H, long long A) {
+  const long long o = c / H;
+  return o * A + (c - o * H);
+}
+
+__device__ __forceinline__ void load_columns(const ColArgs& a, float2* buf, long long c0, int N) {
+  const int TX = a.TX;
+  for (int f = threadIdx.x; f < TX * N; f += blockDim.x) {
+    const int i = f / TX;
+    const int t = f - i * TX;
+    const long long c = c0 + t;
+    const int li = i - a.zoff;
+    float2 v = make_float2(0.f, 0.f);
+    if (c < a.ncols && li >= 0 && li < a.nload) {
+      v = __ldg(a.src + col_offset(c, a.H, a.A) + (long long)li * a.S);
+      if (a.fin_mul != 1.f) v = cscale(v, a.fin_mul);
+    }
+    buf[t * a.pitch + i] = v;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void store_columns(const ColArgs& a, const float2* buf, long long c0, int N) {
+  const int TX = a.TX;
+  for (int f = threadIdx.x; f < TX * N; f += blockDim.x) {
+    const int i = f / TX;
+    const int t = f - i * TX;
+    const long long c = c0 + t;
+    if (c < a.ncols) a.dst[col_offset(c, a.H, a.Ad) + (long long)i * a.Sd] = buf[t * a.pitch + i];
+  }
+}
+
+// Walk the (column, |kz|) pairs of the block's spectrum columns in chunks of
+// BIN_CHUNK consecutive |kz| = m.  k^2 = kx^2 + ky^2 + m^2 grows with m, so the
+// bin index only moves forward inside a chunk.  kz = m and kz = N - m share k^2.
+// Op(t, m, bin, weight) is called for every pair.
+template <typename Op>
+__device__ __forceinline__ void walk_bins(const ColArgs& a, const int32_t* __restrict__ thr, long long c0, Op op) {
+  const int M = a.M, H = a.H, N = a.N;
+  const int nch = (H + BIN_CHUNK - 1) / BIN_CHUNK;
+  const int ntask = a.TX * nch;
+  for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    const int t = task / nch;
+    const int ch = task - t * nch;
+    const long long c = c0 + t;
+    if (c >= a.ncols) continue;
+    const int kyi = (int)(c / H);
+    const int kx = (int)(c - (long long)kyi * H);
+    const int ky = kyi < M ? kyi : kyi - N;
+    const int c2 = kx * kx + ky * ky;
+    const float w = (kx == 0 || kx == M) ? 1.f : 2.f;
+    const int m0 = ch * BIN_CHUNK;
+    const int m1 = min(m0 + BIN_CHUNK, M + 1);
+    int cur = bin_search(thr, a.nbins, c2 + m0 * m0);
+    op.begin(cur);
+    for (int m = m0; m < m1; ++m) {
+      const int s = c2 + m * m;
+      while (cur < a.nbins && thr[cur + 1] <= s) ++cur;
+      op.visit(t, m, cur, w);
+    }
+    op.end(w);
+  }
+}
+
+struct BinAccum {
+  const float2* buf;
+  int pitch, M, N, nbins;
+  float iscale;
+  double* hs;
+  double* hs2;
+  int run;
+  float aI, aI2;
+  __device__ __forceinline__ void flush(float w) {
+    if (run >= 0 && run < nbins && (aI != 0.f || aI2 != 0.f)) {
+      atomicAdd(hs + run, (double)(w * aI));
+      atomicAdd(hs2 + run, (double)(w * aI2));
+    }
+    aI = 0.f;
+    aI2 = 0.f;
+  }
+  __device__ __forceinline__ void begin(int b) {
+    run = b;
+    aI = 0.f;
+    aI2 = 0.f;
+  }
+  __device__ __forceinline__ void visit(int t, int m, int b, float w) {
+    if (b != run) {
+      flush(w);
+      run = b;
+    }
+    const float2 f1 = buf[t * pitch + m];
+    const float i1 = (f1.x * f1.x + f1.y * f1.y) * iscale;
+    float s = i1, s2 = i1 * i1;
+    if (m != 0 && m != M) {
+      const float2 f2 = buf[t * pitch + N - m];
+      const float i2 = (f2.x * f2.x + f2.y * f2.y) * iscale;
+      s += i2;
+      s2 += i2 * i2;
+    }
+    aI += s;
+    aI2 += s2;
+  }
+  __device__ __forceinline__ void end(float w) { flush(w); }
+};
+
+struct SigmaScale {
+  float2* buf;
+  int pitch, M, N, nbins;
+  const float* sigma;
+  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void end(float) {}
+  __device__ __forceinline__ void visit(int t, int m, int b, float) {
+    const float sg = (b >= 0 && b < nbins) ? __ldg(sigma + b) : 0.f;
+    float2* col = buf + t * pitch;
+    col[m] = cscale(col[m], sg);
+    if (m != 0 && m != M) col[N - m] = cscale(col[N - m], sg);
+  }
+};
+
+// One block per tile of TX columns.  (A persistent loop over tiles around the
+// shared-memory FFT made the compiler spill ~1.3 KB per thread.)
+template <int MODE, bool INV>
+__global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_blo, s_bhi;
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  const int N = a.N;
+  const size_t buf_bytes = ur_align_up_dev((size_t)a.TX * a.pitch * sizeof(float2), 16);
+  int32_t* thr = reinterpret_cast<int32_t*>(smraw + buf_bytes);
+  double* hs = nullptr;
+  double* hs2 = nullptr;
+  const long long c0 = (long long)blockIdx.x * a.TX;
+  if (MODE != COL_Y && a.nbins > 0) {
+    for (int j = threadIdx.x; j <= a.nbins; j += blockDim.x) thr[j] = __ldg(a.thr + j);
+    if (MODE == COL_ZBIN) {
+      hs = reinterpret_cast<double*>(smraw + buf_bytes + ur_align_up_dev((size_t)(a.nbins + 1) * 4, 16));
+      hs2 = hs + a.nbins;
+      if (threadIdx.x == 0) {
+        s_blo = 0x7fffffff;
+        s_bhi = -1;
+      }
+    }
+  }
+  __syncthreads();
+  if (MODE == COL_ZBIN && a.nbins > 0) {
+    // bins this tile can reach: k^2 in [min kx^2+ky^2, max kx^2+ky^2 + (N/2)^2]
+    if (threadIdx.x < a.TX && c0 + threadIdx.x < a.ncols) {
+      const long long c = c0 + threadIdx.x;
+      const int kyi = (int)(c / a.H);
+      const int kx = (int)(c - (long long)kyi * a.H);
+      const int ky = kyi < a.M ? kyi : kyi - N;
+      const int c2 = kx * kx + ky * ky;
+      atomicMin(&s_blo, max(bin_search(thr, a.nbins, c2), 0));
+      atomicMax(&s_bhi, min(bin_search(thr, a.nbins, c2 + a.M * a.M), a.nbins - 1));
+    }
+    __syncthreads();
+    for (int j = s_blo + (int)threadIdx.x; j <= s_bhi; j += blockDim.x) {
+      hs[j] = 0.0;
+      hs2[j] = 0.0;
+    }
+  }
+  {
+    load_columns(a, buf, c0, N);
+    if (MODE == COL_Y) {
+      fft_lines<INV, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      store_columns(a, buf, c0, N);
+    } else if (MODE == COL_ZBIN) {
+      fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      if (a.fout) {
+        for (int f = threadIdx.x; f < a.TX * N; f += blockDim.x) {
+          const int i = f / a.TX;
+          const int t = f - i * a.TX;
+          const long long c = c0 + t;
+          if (c < a.ncols) a.fout[(long long)i * N * a.H + c] = cscale(buf[t * a.pitch + i], a.fscale);
+        }
+      }
+      if (a.nbins > 0) {
+        BinAccum acc{buf, a.pitch, a.M, N, a.nbins, a.iscale, hs, hs2, -1, 0.f, 0.f};
+        walk_bins(a, thr, c0, acc);
+      }
+    } else {  // COL_ZADJ: F along z (recomputed or given), times sigma(bin), inverse along z
+      if (!a.skip_fwd) fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      SigmaScale sc{buf, a.pitch, a.M, N, a.nbins, a.sigma};
+      walk_bins(a, thr, c0, sc);
+      __syncthreads();
+      fft_lines<true, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      store_columns(a, buf, c0, N);
+    }
+  }
+  if (MODE == COL_ZBIN && a.nbins > 0) {
+    __syncthreads();
+    for (int j = s_blo + (int)threadIdx.x; j <= s_bhi; j += blockDim.x) {
+      if (hs[j] != 0.0) atomicAdd(a.gsum + j, hs[j]);
+      if (hs2[j] != 0.0) atomicAdd(a.gsum2 + j, hs2[j]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: bins[UR_BIN_FIELDS][B] from the accumulated sums (in I' units:
+// I' = N^3 I) and the plan's per-bin count and sum |Q|.
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(double* __restrict__ bins, const double* __restrict__ geo, int nb, double inv_n3) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double n = geo[j];
+  const double s = bins[UR_BIN_SUM_I * nb + j] * inv_n3;
+  const double s2 = bins[UR_BIN_SUM_I2 * nb + j] * (inv_n3 * inv_n3);
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  bins[UR_BIN_COUNT * nb + j] = n;
+  bins[UR_BIN_SUM_I * nb + j] = s;
+  bins[UR_BIN_SUM_I2 * nb + j] = s2;
+  bins[UR_BIN_SUM_Q * nb + j] = geo[nb + j];
+  double mean = nan, sem = nan;
+  if (n > 0) mean = s / n;
+  if (n > 1) {
+    double var = (s2 - s * mean) / (n - 1.0);
+    if (var < 0) var = 0;
+    sem = sqrt(var / n);
+  }
+  bins[UR_BIN_MEAN * nb + j] = mean;
+  bins[UR_BIN_SEM * nb + j] = sem;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time bin geometry: count (weighted by the half-spectrum multiplicity)
+// and sum of |Q| per bin over the full N^3 grid; independent of the data.
+// One thread per (ky, kx) column, walking |kz| = m; block histogram in shared
+// memory, then one global add per touched bin.
+// ---------------------------------------------------------------------------
+__global__ void k_geometry(const int32_t* __restrict__ thr_g, int nb, int N, double dq,
+                           unsigned long long* __restrict__ gcount, double* __restrict__ gsumq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int32_t* thr = reinterpret_cast<int32_t*>(smraw);
+  unsigned long long* hc = reinterpret_cast<unsigned long long*>(smraw + ur_align_up_dev((size_t)(nb + 1) * 4, 16));
+  double* hq = reinterpret_cast<double*>(hc + nb);
+  for (int j = threadIdx.x; j <= nb; j += blockDim.x) thr[j] = thr_g[j];
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    hc[j] = 0ull;
+    hq[j] = 0.0;
+  }
+  __syncthreads();
+  const int M = N / 2, H = M + 1;
+  const long long ncols = (long long)N * H;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += (long long)gridDim.x * blockDim.x) {
+    const int kyi = (int)(c / H);
+    const int kx = (int)(c - (long long)kyi * H);
+    const int ky = kyi < M ? kyi : kyi - N;
+    const int c2 = kx * kx + ky * ky;
+    const unsigned long long w = (kx == 0 || kx == M) ? 1ull : 2ull;
+    int cur = bin_search(thr, nb, c2);
+    int run = cur;
+    unsigned long long cnt = 0;
+    double sq = 0.0;
+    for (int m = 0; m <= M; ++m) {
+      const int s = c2 + m * m;
+      while (cur < nb && thr[cur + 1] <= s) ++cur;
+      if (cur != run) {
+        if (run >= 0 && run < nb && cnt) {
+          atomicAdd(hc + run, cnt * w);
+          atomicAdd(hq + run, sq * (double)w);
+        }
+        run = cur;
+        cnt = 0;
+        sq = 0.0;
+      }
+      const unsigned long long mult = (m == 0 || m == M) ? 1ull : 2ull;
+      cnt += mult;
+      sq += (double)mult * sqrt((double)s);
+    }
+    if (run >= 0 && run < nb && cnt) {
+      atomicAdd(hc + run, cnt * w);
+      atomicAdd(hq + run, sq * (double)w);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    if (hc[j]) {
+      atomicAdd(gcount + j, hc[j]);
+      atomicAdd(gsumq + j, hq[j] * dq);
+    }
+  }
+}
+
+__global__ void k_geo_to_double(const unsigned long long* __restrict__ c, double* __restrict__ out, int nb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) out[j] = (double)c[j];
+}
+
+ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s) {
+  const int nb = p->nbins;
+  unsigned long long* cnt = nullptr;
+  UR_CUDA_CHECK(cudaMalloc(&cnt, sizeof(unsigned long long) * nb));
+  UR_CUDA_CHECK(cudaMemset(cnt, 0, sizeof(unsigned long long) * nb));
+  UR_CUDA_CHECK(cudaMemset(p->geo, 0, sizeof(double) * 2 * nb));
+  const size_t smem = ur_align_up((size_t)(nb + 1) * 4, 16) + (size_t)nb * 16;
+  if (smem > 48 * 1024) UR_CUDA_CHECK(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long ncols = (long long)p->n * p->H;
+  long long blocks = (ncols + 255) / 256;
+  const long long cap = (long long)p->num_sms * 4;
+  if (blocks > cap) blocks = cap;
+  k_geometry<<<(int)blocks, 256, smem, s>>>(p->thr, nb, p->n, p->dq, cnt, p->geo + nb);
+  UR_LAUNCH_CHECK("k_geometry");
+  k_geo_to_double<<<(nb + 255) / 256, 256, 0, s>>>(cnt, p->geo, nb);
+  UR_LAUNCH_CHECK("k_geo_to_double");
+  UR_CUDA_CHECK(cudaStreamSynchronize(s));
+  UR_CUDA_CHECK(cudaFree(cnt));
+  return UR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Standalone binning of a stored half-spectrum intensity (Sec. 2.5)
+// ---------------------------------------------------------------------------
+__global__ void k_bin_half(const float* __restrict__ I, int N, const int32_t* __restrict__ thr_g, int nb,
+                           double* __restrict__ gsum, double* __restrict__ gsum2, double scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int32_t* thr = reinterpret_cast<int32_t*>(smraw);
+  double* hs = reinterpret_cast<double*>(smraw + ur_align_up_dev((size_t)(nb + 1) * 4, 16));
+  double* hs2 = hs + nb;
+  for (int j = threadIdx.x; j <= nb; j += blockDim.x) thr[j] = thr_g[j];
+  for (int j = threadIdx.x; j < 2 * nb; j += blockDim.x) hs[j] = 0.0;
+  __syncthreads();
+  const int M = N / 2, H = M + 1;
+  const long long total = (long long)N * N * H;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e % ((long long)N * H);
+    const int kzi = (int)(e / ((long long)N * H));
+    const int kyi = (int)(c / H);
+    const int kx = (int)(c - (long long)kyi * H);
+    const int ky = kyi < M ? kyi : kyi - N;
+    const int kz = kzi < M ? kzi : kzi - N;
+    const int s = kx * kx + ky * ky + kz * kz;
+    const int b = bin_search(thr, nb, s);
+    if (b >= 0 && b < nb) {
+      const double w = (kx == 0 || kx == M) ? 1.0 : 2.0;
+      const double v = (double)I[e] * scale;
+      atomicAdd(hs + b, w * v);
+      atomicAdd(hs2 + b, w * v * v);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    if (hs[j] != 0.0) atomicAdd(gsum + j, hs[j]);
+    if (hs2[j] != 0.0) atomicAdd(gsum2 + j, hs2[j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host: kernel configuration for a plan
+// ---------------------------------------------------------------------------
+size_t ur_colbin_smem(const ur_plan* p) {
+  return ur_align_up((size_t)p->col_tx * (p->n + 1) * sizeof(float2), 16) + ur_align_up((size_t)(p->nbins + 1) * 4, 16) +
+         (size_t)p->nbins * 16;
+}
+
+ur_status ur_configure_kernels(ur_plan* p) {
+  const int n = p->n, M = p->M;
+  // rows: RB rows of M complex per block, 256 threads, <= EMAX elements per thread
+  p->row_threads = 256;
+  p->row_rb = (UR_EMAX * p->row_threads) / M;
+  if (p->row_rb > 64) p->row_rb = 64;
+  if (p->row_rb < 1) p->row_rb = 1;
+  p->row_smem = (size_t)p->row_rb * M * sizeof(float2);
+  // columns: TX columns of N complex per block
+  p->col_threads = 256;
+  p->col_tx = (UR_EMAX * p->col_threads) / n;
+  if (p->col_tx > 64) p->col_tx = 64;
+  if (p->col_tx < 1) p->col_tx = 1;
+  p->col_smem = ur_align_up((size_t)p->col_tx * (n + 1) * sizeof(float2), 16) + ur_align_up((size_t)(p->nbins + 1) * 4, 16);
+  p->colbin_smem = ur_colbin_smem(p);
+  if (p->colbin_smem > 227 * 1024) {
+    ur_set_error("ur_plan_create: %d bins need %zu bytes of shared memory per block (max 227 KB)", p->nbins, p->colbin_smem);
+    return UR_ERR_UNSUPPORTED;
+  }
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZBIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->colbin_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZADJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
+  const long long ntiles = ((long long)n * p->H + p->col_tx - 1) / p->col_tx;
+  p->zbin_grid = (int)ntiles;
+  // device copy of the radix schedules
+  UR_CUDA_CHECK(cudaMalloc(&p->d_sched, sizeof(StageInfo) * 2 * UR_MAX_STAGES));
+  UR_CUDA_CHECK(cudaMemcpy(p->d_sched, p->sched_n.st, sizeof(StageInfo) * UR_MAX_STAGES, cudaMemcpyHostToDevice));
+  UR_CUDA_CHECK(cudaMemcpy(p->d_sched + UR_MAX_STAGES, p->sched_m.st, sizeof(StageInfo) * UR_MAX_STAGES, cudaMemcpyHostToDevice));
+  // workspace regions
+  p->ws_inter = (size_t)p->nz * n * p->H * sizeof(float2);
+  p->ws_inv = (size_t)n * n * p->H * sizeof(float2);
+  p->ws_sigma = (size_t)p->nbins * sizeof(float);
+  p->slab_planes = 0;
+  p->ws_slab = 0;
+  return UR_OK;
+}
+
+ur_status ur_launch_cols(int mode, bool inv, const ur_plan* p, const ColArgs& a, int grid, size_t smem, cudaStream_t s) {
+  (void)p;
+  if (grid <= 0) return UR_OK;
+  if (mode == COL_Y && !inv) k_cols<COL_Y, false><<<grid, p->col_threads, smem, s>>>(a);
+  else if (mode == COL_Y) k_cols<COL_Y, true><<<grid, p->col_threads, smem, s>>>(a);
+  else if (mode == COL_ZBIN) k_cols<COL_ZBIN, false><<<grid, p->col_threads, smem, s>>>(a);
+  else k_cols<COL_ZADJ, false><<<grid, p->col_threads, smem, s>>>(a);
+  UR_LAUNCH_CHECK("k_cols");
+  return UR_OK;
+}
+
+ColArgs ur_col_args(const ur_plan* p) {
+  ColArgs a;
+  memset(&a, 0, sizeof a);
+  a.N = p->n;
+  a.H = p->H;
+  a.M = p->M;
+  a.TX = p->col_tx;
+  a.pitch = p->n + 1;
+  a.sched = p->d_sched;
+  a.nst = p->sched_n.nst;
+  a.tw = p->tw;
+  a.thr = p->thr;
+  a.nbins = p->nbins;
+  a.fin_mul = 1.f;
+  return a;
+}
+
+// Pass 1 over rows [0, nrows) of a slab of planes `ed` into X (same plane order).
+ur_status ur_plane_pass(const ur_plan* p, const void* ed, long long nplanes, float2* X, cudaStream_t s) {
+  const long long nrows = nplanes * p->n;
+  const int grid_rows = (int)((nrows + p->row_rb - 1) / p->row_rb);
+  const StageInfo* sm = p->d_sched + UR_MAX_STAGES;
+  ur_timing_begin("rows_r2c", s);
+  if (p->ed_dtype == UR_F32)
+    k_rows_r2c<float><<<grid_rows, p->row_threads, p->row_smem, s>>>((const float*)ed, X, nrows, p->n, p->row_rb, sm,
+                                                                     p->sched_m.nst, p->tw);
+  else
+    k_rows_r2c<__half><<<grid_rows, p->row_threads, p->row_smem, s>>>((const __half*)ed, X, nrows, p->n, p->row_rb, sm,
+                                                                      p->sched_m.nst, p->tw);
+  UR_LAUNCH_CHECK("k_rows_r2c");
+  ur_timing_end(s);
+  ColArgs a = ur_col_args(p);
+  a.src = X;
+  a.dst = X;
+  a.ncols = nplanes * p->H;
+  a.A = (long long)p->n * p->H;
+  a.S = p->H;
+  a.Ad = a.A;
+  a.Sd = a.S;
+  a.nload = p->n;
+  a.zoff = 0;
+  a.nbins = 0;
+  const long long ntiles = (a.ncols + a.TX - 1) / a.TX;
+  ur_timing_begin("cols_y", s);
+  k_cols<COL_Y, false><<<(int)ntiles, p->col_threads, p->col_smem, s>>>(a);
+  UR_LAUNCH_CHECK("k_cols<COL_Y>");
+  ur_timing_end(s);
+  return UR_OK;
+}
+
+// Pass 2 (+ binning) from the intermediate X holding planes [z0, z0+nz).
+ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2* F_out, cudaStream_t s) {
+  const int nb = p->nbins;
+  ColArgs a = ur_col_args(p);
+  a.src = X;
+  a.ncols = (long long)p->n * p->H;
+  a.A = p->H;
+  a.S = (long long)p->n * p->H;
+  a.nload = p->nz;
+  a.zoff = p->z0;
+  const double n3 = (double)p->n * p->n * p->n;
+  a.iscale = (float)(1.0 / n3);
+  a.fout = F_out;
+  a.fscale = (float)(1.0 / n3);
+  if (bins) {
+    UR_CUDA_CHECK(cudaMemsetAsync(bins, 0, sizeof(double) * UR_BIN_FIELDS * nb, s));
+    a.gsum = bins + UR_BIN_SUM_I * nb;
+    a.gsum2 = bins + UR_BIN_SUM_I2 * nb;
+  } else {
+    a.nbins = 0;
+  }
+  ur_timing_begin("cols_z_bin", s);
+  k_cols<COL_ZBIN, false><<<p->zbin_grid, p->col_threads, p->colbin_smem, s>>>(a);
+  UR_LAUNCH_CHECK("k_cols<COL_ZBIN>");
+  ur_timing_end(s);
+  if (bins) {
+    ur_timing_begin("finalize", s);
+    k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
+    UR_LAUNCH_CHECK("k_finalize");
+    ur_timing_end(s);
+  }
+  return UR_OK;
+}
+
+extern "C" ur_status ur_fft_intensity(const ur_plan* p, const void* ed, int32_t ed_on_host, double* bins, void* F_out,
+                                      void* ws, size_t ws_bytes, void* stream) {
+  UR_REQUIRE(p && ed && ws, "ur_fft_intensity: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ed_on_host) return ur_fft_intensity_host(p, ed, bins, (float2*)F_out, ws, ws_bytes, s);
+  UR_REQUIRE(ws_bytes >= ur_workspace_size(p, UR_WS_FORWARD), "ur_fft_intensity: workspace %zu < %zu bytes", ws_bytes,
+             ur_workspace_size(p, UR_WS_FORWARD));
+  UR_REQUIRE(((uintptr_t)ed % 8) == 0 && ((uintptr_t)ws % 256) == 0, "ur_fft_intensity: misaligned ed or ws");
+  UR_TRY(ur_fault_point("fft_intensity"));
+  float2* X = (float2*)ws;
+  UR_TRY(ur_plane_pass(p, ed, p->nz, X, s));
+  UR_TRY(ur_column_pass(p, X, bins, (float2*)F_out, s));
+  return UR_OK;
+}
+
+extern "C" ur_status ur_bin_q(const ur_plan* p, const float* I, double* bins, void* ws, size_t ws_bytes, void* stream) {
+  UR_REQUIRE(p && I && bins, "ur_bin_q: null argument");
+  (void)ws;
+  (void)ws_bytes;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = p->nbins;
+  const size_t smem = ur_align_up((size_t)(nb + 1) * 4, 16) + (size_t)nb * 16;
+  if (smem > 48 * 1024) UR_CUDA_CHECK(cudaFuncSetAttribute(k_bin_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  UR_CUDA_CHECK(cudaMemsetAsync(bins, 0, sizeof(double) * UR_BIN_FIELDS * nb, s));
+  const double n3 = (double)p->n * p->n * p->n;
+  // the kernel accumulates I * N^3 so that k_finalize's I' convention applies
+  k_bin_half<<<p->num_sms * 4, 256, smem, s>>>(I, p->n, p->thr, nb, bins + UR_BIN_SUM_I * nb, bins + UR_BIN_SUM_I2 * nb, n3);
+  UR_LAUNCH_CHECK("k_bin_half");
+  k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
+  UR_LAUNCH_CHECK("k_finalize");
+  return UR_OK;
+}

@@ -1,0 +1,51 @@
+// Declarations shared by the forward, adjoint, out-of-core and batched
+// translation units.
+#pragma once
+
+#include "ur_common.cuh"
+
+#define UR_EMAX 16  // elements per thread in the shared-memory FFT engine
+
+enum { COL_Y = 0, COL_ZBIN = 1, COL_ZADJ = 2 };
+
+__host__ __device__ inline size_t ur_align_up_dev(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct ColArgs {
+  const float2* src;
+  float2* dst;
+  long long ncols;
+  int N, H, M;
+  long long A;       // source offset per outer index (c / H)
+  long long S;       // source stride between column elements
+  long long Ad, Sd;  // destination offset per outer index / element stride
+  int nload;         // elements per column read from src
+  int zoff;          // position of the first loaded element in the column
+  int TX;            // columns per block
+  int pitch;         // shared-memory pitch between columns (float2)
+  const StageInfo* sched;
+  int nst;
+  const float2* tw;
+  // binning
+  const int32_t* thr;
+  int nbins;
+  float iscale;      // I' = |F~|^2 * iscale (I' = N^3 I)
+  double* gsum;      // [nbins] sum of w I'
+  double* gsum2;     // [nbins] sum of w I'^2
+  float2* fout;      // optional F half spectrum [kz][ky][kx]
+  float fscale;
+  // adjoint
+  const float* sigma;  // per-bin scale of F~ along z (adjoint)
+  float fin_mul;       // multiplier applied to every loaded element
+  int skip_fwd;        // 1: the loaded column is already the spectrum along z
+};
+
+ColArgs ur_col_args(const ur_plan* p);
+ur_status ur_plane_pass(const ur_plan* p, const void* ed, long long nplanes, float2* X, cudaStream_t s);
+ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2* F_out, cudaStream_t s);
+ur_status ur_fft_intensity_host(const ur_plan* p, const void* ed_host, double* bins, float2* F_out, void* ws,
+                                size_t ws_bytes, cudaStream_t s);
+ur_status ur_launch_cols(int mode, bool inv, const ur_plan* p, const ColArgs& a, int grid, size_t smem, cudaStream_t s);
+
+// per-kernel event timing (enabled by ur_set_timing)
+void ur_timing_begin(const char* name, cudaStream_t s);
+void ur_timing_end(cudaStream_t s);

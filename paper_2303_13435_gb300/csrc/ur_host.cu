@@ -1,0 +1,426 @@
+// Host side of libur: errors, fault injection, plans (twiddles, bin tables,
+// launch configuration), workspace sizes, and the level merge.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "ur_forward.cuh"
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[1024] = "";
+
+void ur_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* ur_last_error(void) { return g_err; }
+extern "C" const char* ur_version(void) { return "libur 0.1 (sm_103a)"; }
+
+// Host-side fault injection for failure-path tests: UR_FAULT="<site>:<k>"
+// makes the k-th (1-based) pass through fault point <site> fail with
+// UR_ERR_FAULT_INJECTED.  Nothing on the device is faulted.
+static std::mutex g_fault_mu;
+static std::string g_fault_site;
+static long g_fault_target = -1;
+static long g_fault_count = 0;
+static bool g_fault_loaded = false;
+
+ur_status ur_fault_point(const char* site) {
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  if (!g_fault_loaded) {
+    g_fault_loaded = true;
+    const char* env = getenv("UR_FAULT");
+    if (env && *env) {
+      const char* colon = strrchr(env, ':');
+      if (colon) {
+        g_fault_site.assign(env, colon - env);
+        g_fault_target = atol(colon + 1);
+      } else {
+        g_fault_site = env;
+        g_fault_target = 1;
+      }
+    }
+  }
+  if (g_fault_target > 0 && g_fault_site == site) {
+    if (++g_fault_count == g_fault_target) {
+      ur_set_error("fault injected at %s (pass %ld)", site, g_fault_count);
+      return UR_ERR_FAULT_INJECTED;
+    }
+  }
+  return UR_OK;
+}
+
+extern "C" void ur_fault_reset(void) {
+  std::lock_guard<std::mutex> lk(g_fault_mu);
+  g_fault_loaded = false;
+  g_fault_site.clear();
+  g_fault_target = -1;
+  g_fault_count = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Per-kernel event timing (measurement aid; off by default).  Each internal
+// launch is bracketed by two events on its own stream; ur_last_timings waits
+// for them and reports the accumulated entries of the calling thread.
+// ---------------------------------------------------------------------------
+struct TimingSlot {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static thread_local bool g_timing = false;
+static thread_local TimingSlot* g_slots = nullptr;
+static thread_local int g_nslots = 0, g_used = 0;
+
+extern "C" void ur_set_timing(int32_t enable) {
+  g_timing = enable != 0;
+  g_used = 0;
+}
+
+void ur_timing_begin(const char* name, cudaStream_t s) {
+  if (!g_timing) return;
+  if (g_used == g_nslots) {
+    int nn = g_nslots ? 2 * g_nslots : 64;
+    TimingSlot* ns = (TimingSlot*)realloc(g_slots, sizeof(TimingSlot) * nn);
+    if (!ns) return;
+    for (int i = g_nslots; i < nn; ++i) {
+      cudaEventCreate(&ns[i].a);
+      cudaEventCreate(&ns[i].b);
+    }
+    g_slots = ns;
+    g_nslots = nn;
+  }
+  g_slots[g_used].name = name;
+  cudaEventRecord(g_slots[g_used].a, s);
+}
+
+void ur_timing_end(cudaStream_t s) {
+  if (!g_timing || g_used >= g_nslots) return;
+  cudaEventRecord(g_slots[g_used].b, s);
+  ++g_used;
+}
+
+extern "C" int32_t ur_last_timings(float* ms_out, int32_t max_entries, const char** names_out) {
+  int n = 0;
+  for (int i = 0; i < g_used && n < max_entries; ++i, ++n) {
+    cudaEventSynchronize(g_slots[i].b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g_slots[i].a, g_slots[i].b);
+    if (ms_out) ms_out[n] = ms;
+    if (names_out) names_out[n] = g_slots[i].name;
+  }
+  g_used = 0;
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// Radix schedules
+// ---------------------------------------------------------------------------
+bool ur_make_sched(int L, int n_tab, Sched* out) {
+  memset(out, 0, sizeof *out);
+  out->L = L;
+  int rad[64];
+  int nr = 0;
+  int r = L;
+  while (r % 8 == 0) { rad[nr++] = 8; r /= 8; }
+  while (r % 4 == 0) { rad[nr++] = 4; r /= 4; }
+  while (r % 2 == 0) { rad[nr++] = 2; r /= 2; }
+  while (r % 3 == 0) { rad[nr++] = 3; r /= 3; }
+  while (r % 5 == 0) { rad[nr++] = 5; r /= 5; }
+  while (r % 7 == 0) { rad[nr++] = 7; r /= 7; }
+  if (r != 1 || nr > UR_MAX_STAGES || n_tab % L != 0) return false;
+  int Ns = 1;
+  for (int i = 0; i < nr; ++i) {
+    StageInfo& si = out->st[i];
+    si.R = rad[i];
+    si.nb = L / rad[i];
+    si.Ns = Ns;
+    si.tstep = n_tab / (Ns * rad[i]);
+    si.div_nb = FastDiv((uint32_t)si.nb);
+    si.div_ns = FastDiv((uint32_t)Ns);
+    Ns *= rad[i];
+  }
+  out->nst = nr;
+  return true;
+}
+
+// Exported self-check of the integer division used by the kernels (host build
+// of the same code); returns the number of mismatches.
+extern "C" int64_t ur_selftest_fastdiv(void) {
+  int64_t bad = 0;
+  const uint32_t ds[] = {1, 2, 3, 5, 6, 7, 9, 10, 12, 14, 17, 31, 49, 96, 100, 125, 127, 129, 243, 257,
+                         343, 385, 1000, 1025, 2049, 4097, 65537, 1000003};
+  for (uint32_t d : ds) {
+    FastDiv f(d);
+    for (uint32_t x = 0; x < 70000; ++x)
+      if (f.div(x) != x / d) ++bad;
+    for (uint32_t x = (1u << 31) - 70000; x < (1u << 31); ++x)
+      if (f.div(x) != x / d) ++bad;
+  }
+  return bad;
+}
+
+// ---------------------------------------------------------------------------
+// Bin thresholds: t_j = min{s >= 0 : dq * sqrt(s) >= e_j} for j < B and
+// t_B = min{s : dq * sqrt(s) > e_B}, in IEEE float64.  fl(dq * fl(sqrt(s))) is
+// nondecreasing in s, so a binary search finds the exact crossing of the same
+// float64 expression a per-voxel evaluation would use.
+// ---------------------------------------------------------------------------
+static inline double q_of(double dq, int64_t s) { return dq * sqrt((double)s); }
+
+static int64_t first_s(double dq, double e, int64_t smax, bool strict) {
+  int64_t lo = 0, hi = smax + 1;  // answer in [lo, hi]; hi = none
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    double q = q_of(dq, mid);
+    bool ok = strict ? (q > e) : (q >= e);
+    if (ok) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+extern "C" ur_status ur_bin_thresholds(int32_t n, double dx, const double* edges, int32_t nbins, int64_t* out) {
+  UR_REQUIRE(n >= 2 && dx > 0 && edges && out && nbins >= 1, "ur_bin_thresholds: bad argument");
+  const double dq = 2.0 * M_PI / ((double)n * dx);
+  const int64_t smax = 3ll * (n / 2) * (n / 2);
+  for (int j = 0; j <= nbins; ++j) out[j] = first_s(dq, edges[j], smax, j == nbins);
+  return UR_OK;
+}
+
+static bool smooth_2357(int v) {
+  if (v <= 0) return false;
+  for (int p : {2, 3, 5, 7})
+    while (v % p == 0) v /= p;
+  return v == 1;
+}
+
+static void plan_free(ur_plan* p) {
+  if (!p) return;
+  if (p->tw) cudaFree(p->tw);
+  if (p->thr) cudaFree(p->thr);
+  if (p->geo) cudaFree(p->geo);
+  if (p->d_sched) cudaFree(p->d_sched);
+  free(p->thr_host);
+  free(p);
+}
+
+template <typename K>
+static int occupancy(K kern, int threads, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
+// defined in ur_forward.cu: configures the kernels for a plan
+ur_status ur_configure_kernels(ur_plan* p);
+
+extern "C" ur_status ur_plan_create(const ur_grid_desc* g, const double* edges, int32_t nbins, ur_plan** out) {
+  UR_REQUIRE(g && edges && out, "ur_plan_create: null argument");
+  *out = nullptr;
+  const int n = g->n;
+  UR_REQUIRE(n >= 8 && n <= 4096 && n % 2 == 0 && smooth_2357(n / 2),
+             "ur_plan_create: grid edge %d must be even, in [8, 4096], with N/2 a product of 2, 3, 5, 7", n);
+  UR_REQUIRE(g->dx > 0 && isfinite(g->dx), "ur_plan_create: dx must be positive");
+  UR_REQUIRE(g->ed_dtype == UR_F32 || g->ed_dtype == UR_F16, "ur_plan_create: ed_dtype must be UR_F32 or UR_F16");
+  UR_REQUIRE(g->z0 >= 0 && g->nz >= 1 && g->z0 + g->nz <= n, "ur_plan_create: plane range [%d, %d) outside [0, %d)",
+             g->z0, g->z0 + g->nz, n);
+  UR_REQUIRE(nbins >= 1 && nbins <= 8192, "ur_plan_create: nbins %d outside [1, 8192]", nbins);
+  for (int j = 0; j <= nbins; ++j) UR_REQUIRE(isfinite(edges[j]), "ur_plan_create: edge %d not finite", j);
+  for (int j = 0; j < nbins; ++j) UR_REQUIRE(edges[j] < edges[j + 1], "ur_plan_create: edges must increase strictly");
+  UR_TRY(ur_fault_point("plan_create"));
+
+  ur_plan* p = (ur_plan*)calloc(1, sizeof(ur_plan));
+  if (!p) {
+    ur_set_error("ur_plan_create: out of host memory");
+    return UR_ERR_OOM;
+  }
+  p->n = n;
+  p->M = n / 2;
+  p->H = n / 2 + 1;
+  p->dx = g->dx;
+  p->dq = 2.0 * M_PI / ((double)n * g->dx);
+  p->ed_dtype = g->ed_dtype;
+  p->z0 = g->z0;
+  p->nz = g->nz;
+  p->nbins = nbins;
+  cudaGetDevice(&p->device);
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (p->num_sms <= 0) p->num_sms = 1;
+
+  if (!ur_make_sched(n, n, &p->sched_n) || !ur_make_sched(p->M, n, &p->sched_m)) {
+    plan_free(p);
+    ur_set_error("ur_plan_create: no radix schedule for %d", n);
+    return UR_ERR_INVALID;
+  }
+
+  // twiddles exp(-2 pi i t / n), float64 -> float32
+  float2* tw_h = (float2*)malloc(sizeof(float2) * n);
+  for (int t = 0; t < n; ++t) {
+    double a = 2.0 * M_PI * (double)t / (double)n;
+    tw_h[t] = make_float2((float)cos(a), (float)(-sin(a)));
+  }
+  // thresholds
+  const int64_t smax = 3ll * (n / 2) * (n / 2);
+  p->thr_host = (int64_t*)malloc(sizeof(int64_t) * (nbins + 1));
+  int32_t* thr32 = (int32_t*)malloc(sizeof(int32_t) * (nbins + 1));
+  for (int j = 0; j <= nbins; ++j) {
+    int64_t t = first_s(p->dq, edges[j], smax, j == nbins);
+    p->thr_host[j] = t;
+    thr32[j] = (int32_t)(t > smax + 1 ? smax + 1 : t);
+  }
+  cudaError_t e1 = cudaMalloc(&p->tw, sizeof(float2) * n);
+  cudaError_t e2 = cudaMalloc(&p->thr, sizeof(int32_t) * (nbins + 1));
+  cudaError_t e3 = cudaMalloc(&p->geo, sizeof(double) * 2 * nbins);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    free(tw_h);
+    free(thr32);
+    plan_free(p);
+    ur_set_error("ur_plan_create: device allocation of plan tables failed");
+    return UR_ERR_OOM;
+  }
+  cudaError_t e4 = cudaMemcpy(p->tw, tw_h, sizeof(float2) * n, cudaMemcpyHostToDevice);
+  cudaError_t e5 = cudaMemcpy(p->thr, thr32, sizeof(int32_t) * (nbins + 1), cudaMemcpyHostToDevice);
+  free(tw_h);
+  free(thr32);
+  if (e4 != cudaSuccess || e5 != cudaSuccess) {
+    plan_free(p);
+    ur_set_error("ur_plan_create: copy of plan tables failed: %s", cudaGetErrorString(e4 != cudaSuccess ? e4 : e5));
+    return UR_ERR_CUDA;
+  }
+  ur_status st = ur_configure_kernels(p);
+  if (st != UR_OK) {
+    plan_free(p);
+    return st;
+  }
+  // data-independent bin geometry (count and sum |Q| per bin)
+  st = ur_launch_geometry(p, 0);
+  if (st == UR_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      ur_set_error("ur_plan_create: bin geometry kernel failed: %s", cudaGetErrorString(e));
+      st = UR_ERR_CUDA;
+    }
+  }
+  if (st != UR_OK) {
+    plan_free(p);
+    return st;
+  }
+  *out = p;
+  return UR_OK;
+}
+
+extern "C" ur_status ur_plan_destroy(ur_plan* p) {
+  plan_free(p);
+  return UR_OK;
+}
+
+extern "C" ur_status ur_plan_thresholds(const ur_plan* p, int64_t* out) {
+  UR_REQUIRE(p && out, "ur_plan_thresholds: null argument");
+  memcpy(out, p->thr_host, sizeof(int64_t) * (p->nbins + 1));
+  return UR_OK;
+}
+
+extern "C" size_t ur_workspace_size(const ur_plan* p, int32_t what) {
+  if (!p) return 0;
+  size_t b = 0;
+  if (what & (UR_WS_FORWARD | UR_WS_BACKWARD)) b += ur_align_up(p->ws_inter, 256);
+  if (what & UR_WS_BACKWARD) b += ur_align_up(p->ws_inv, 256) + ur_align_up(p->ws_sigma, 256);
+  if (what & UR_WS_HOST_SLABS) b += 2 * ur_align_up(p->ws_slab, 256);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Merge (Sec. 2.5 last paragraph): one thread per output bin.
+// ---------------------------------------------------------------------------
+#define UR_MAX_LEVELS 8
+struct MergeArgs {
+  const double* bins[UR_MAX_LEVELS];
+  double scale[UR_MAX_LEVELS];  // N^6
+  double qlo[UR_MAX_LEVELS];    // window lower edge, in window order
+  double qhi[UR_MAX_LEVELS];
+  int order[UR_MAX_LEVELS];     // level index of the t-th window
+  int nlev;
+};
+
+__global__ void k_merge(MergeArgs a, const double* __restrict__ edges, int nb, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double c = sqrt(edges[j] * edges[j + 1]);
+  int pick = -1;
+  for (int t = 0; t < a.nlev; ++t) {
+    const bool last = t == a.nlev - 1;
+    if ((a.qlo[t] <= c && c < a.qhi[t]) || (last && c == a.qhi[t])) {
+      pick = t;
+      break;
+    }
+  }
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double mean = nan, sem = nan, cnt = 0.0, q = nan, src = -1.0;
+  if (pick >= 0) {
+    const double* b = a.bins[pick];
+    const double n = b[UR_BIN_COUNT * nb + j];
+    if (n > 0) {
+      const double s = a.scale[pick];
+      mean = b[UR_BIN_MEAN * nb + j] * s;
+      sem = b[UR_BIN_SEM * nb + j] * s;
+      cnt = n;
+      q = b[UR_BIN_SUM_Q * nb + j] / n;
+      src = (double)a.order[pick];
+    }
+  }
+  out[0 * nb + j] = mean;
+  out[1 * nb + j] = sem;
+  out[2 * nb + j] = cnt;
+  out[3 * nb + j] = q;
+  out[4 * nb + j] = src;
+}
+
+extern "C" ur_status ur_merge(int32_t nlev, const double* const* level_bins, const int32_t* level_n,
+                              const double* level_qmax, const double* edges, int32_t nbins, double* out,
+                              void* stream) {
+  UR_REQUIRE(nlev >= 1 && nlev <= UR_MAX_LEVELS, "ur_merge: nlev %d outside [1, %d]", nlev, UR_MAX_LEVELS);
+  UR_REQUIRE(level_bins && level_n && level_qmax && edges && out, "ur_merge: null argument");
+  UR_REQUIRE(nbins >= 1, "ur_merge: nbins must be positive");
+  MergeArgs a;
+  memset(&a, 0, sizeof a);
+  a.nlev = nlev;
+  int idx[UR_MAX_LEVELS];
+  for (int i = 0; i < nlev; ++i) {
+    UR_REQUIRE(level_bins[i], "ur_merge: level %d has no bins", i);
+    UR_REQUIRE(level_n[i] > 0 && level_qmax[i] > 0, "ur_merge: level %d has a bad size or window", i);
+    idx[i] = i;
+  }
+  // windows ordered by their upper limit (coarsest level first); stable
+  for (int i = 1; i < nlev; ++i)
+    for (int k = i; k > 0 && level_qmax[idx[k]] < level_qmax[idx[k - 1]]; --k) {
+      int t = idx[k];
+      idx[k] = idx[k - 1];
+      idx[k - 1] = t;
+    }
+  double lo = 0.0;
+  for (int t = 0; t < nlev; ++t) {
+    const int i = idx[t];
+    a.bins[t] = level_bins[i];
+    double nn = (double)level_n[i];
+    a.scale[t] = nn * nn * nn * nn * nn * nn;
+    a.qlo[t] = lo;
+    a.qhi[t] = level_qmax[i];
+    a.order[t] = i;
+    lo = level_qmax[i];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  k_merge<<<(nbins + 127) / 128, 128, 0, s>>>(a, edges, nbins, out);
+  UR_LAUNCH_CHECK("k_merge");
+  return UR_OK;
+}

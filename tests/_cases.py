@@ -1,0 +1,77 @@
+"""Shared helpers of the GPU parity tests: oracle side and comparison rules.
+
+Tolerances (stated here once, used by every parity test):
+* ED voxels, bin counts, bin thresholds: bit-exact.
+* Bin means I(Q): |I_gpu - I_oracle| <= 1e-4 * I_oracle for every bin whose
+  oracle mean is at least 1e-6 of the Parseval mean <I> = sum(rho^2) / N^6.
+  FP32 butterflies carry an absolute error of about eps * log2(N) * rms|F|,
+  so bins far below the mean intensity cannot meet a relative bound; they
+  are counted and reported, not gated.
+* Sum of |Q| per bin: relative 1e-12 (data independent, FP64 on both sides).
+* SEM: relative 1e-3 where the within-bin spread is at least 5 % of the mean
+  and the mean is at least 1e-3 of <I> (the GPU forms it from FP32 sums of I
+  and I^2, so the variance carries the FP32 error of I^2).
+* Gradients: normwise relative error <= 1e-4 against the FP64 oracle.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import adjoint, density, scatter
+
+MEAN_RTOL = 1e-4
+FLOOR = 1e-6
+GRAD_RTOL = 1e-4
+
+
+def oracle_density(w, z_begin=0, z_count=None, out_dtype="f32", weights=None):
+    s = w.shape
+    return density.tile_mask_density(w.n, w.cell, s.kind, s.center, s.size, s.rot, origin=w.origin,
+                                     weights=weights, out_dtype=out_dtype, z_begin=z_begin, z_count=z_count)
+
+
+def parseval_mean(rho64: np.ndarray) -> float:
+    n = rho64.shape[0]
+    return float((rho64 ** 2).sum()) / float(n) ** 6
+
+
+def compare_bins(gpu_bins: np.ndarray, ob: dict, rho64: np.ndarray, label: str = "") -> dict:
+    """Gate GPU bins [6, B] against oracle bins; returns the error report."""
+    cnt = gpu_bins[0]
+    assert np.array_equal(cnt.astype(np.int64), ob["count"]), f"{label}: counts differ"
+    nz = ob["count"] > 0
+    sq_ref = ob["mean_q"] * ob["count"]
+    assert np.allclose(gpu_bins[3][nz], sq_ref[nz], rtol=1e-12, atol=0), f"{label}: sum |Q| differs"
+    mean_g = gpu_bins[4]
+    mean_o = ob["mean"]
+    floor = FLOOR * parseval_mean(rho64)
+    gate = nz & (mean_o >= floor)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rel = np.abs(mean_g - mean_o) / np.abs(mean_o)
+    worst = float(np.nanmax(rel[gate])) if gate.any() else 0.0
+    assert worst <= MEAN_RTOL, f"{label}: max rel err {worst:.3e} over {gate.sum()} gated bins"
+    assert np.all(np.isnan(mean_g[~nz])), f"{label}: empty bins must be NaN"
+    # SEM where the spread is resolvable
+    sem_o = ob["sem"]
+    spread = sem_o * np.sqrt(np.maximum(ob["count"], 1)) / np.where(mean_o > 0, mean_o, np.inf)
+    sgate = gate & (ob["count"] > 1) & (spread >= 0.05) & (mean_o >= 1e-3 * parseval_mean(rho64))
+    if sgate.any():
+        srel = np.abs(gpu_bins[5][sgate] - sem_o[sgate]) / sem_o[sgate]
+        assert float(srel.max()) <= 1e-3, f"{label}: SEM rel err {srel.max():.3e}"
+    return {"gated": int(gate.sum()), "excluded": int((nz & ~gate).sum()), "max_rel_gated": worst,
+            "max_rel_all": float(np.nanmax(rel[nz])) if nz.any() else 0.0}
+
+
+def oracle_forward(rho, dx, edges):
+    return scatter.forward(np.asarray(rho, dtype=np.float64), dx, edges)
+
+
+def normwise(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_grads(rho64, cell, mask, dx, edges, g, count, origin=(0, 0, 0)):
+    grho = adjoint.grad_rho(rho64, dx, edges, g, count=count)
+    return adjoint.grad_cell_and_mask(grho, cell, mask, origin)

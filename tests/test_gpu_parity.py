@@ -1,0 +1,257 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Sizes span several FFT tiles and ragged tails; grid edges cover radices
+2, 3, 5 and 7.  Tolerances are stated in tests/_cases.py.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint, density, merge as omerge, scatter
+from paper_2303_13435_gb300 import api, build, inputs
+
+from _cases import (GRAD_RTOL, compare_bins, normwise, oracle_density, oracle_forward, oracle_grads)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    api.lib()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def mof(n, diameter_vox, nbins=96, seed=0, ucell=64, a_nm=2.6, kind=inputs.SHAPE_SPHERE, rot_seed=None,
+        origin=(0, 0, 0)):
+    w = inputs.mof_workload(n=n, diameter_nm=diameter_vox * a_nm / ucell, nbins=nbins, seed=seed, ucell=ucell,
+                            a_nm=a_nm)
+    if kind != inputs.SHAPE_SPHERE or rot_seed is not None:
+        rot = inputs.random_rotation(inputs.SplitMix64(rot_seed or 1))
+        c = float(n // 2)
+        size = 0.5 * diameter_vox if kind != inputs.SHAPE_CUBE else 0.5 * diameter_vox / math.sqrt(3)
+        w.shape = inputs.Shape(kind, (c, c, c), float(np.float32(size)), rot)
+    w.origin = origin
+    return w
+
+
+def z_range(rho):
+    lo, hi = density.nonzero_plane_range(rho)
+    return lo, hi - lo + 1
+
+
+# ---------------------------------------------------------------------------
+# ED generation: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["sc64", "mof96_origin", "cube_rot", "octa_rot", "all"])
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_density_bit_exact(case, dtype):
+    if case == "sc64":
+        w = inputs.sc64_workload()
+    elif case == "mof96_origin":
+        w = mof(96, 60, origin=(3, 5, 7))
+    elif case == "cube_rot":
+        w = mof(100, 70, kind=inputs.SHAPE_CUBE, rot_seed=5)
+    elif case == "octa_rot":
+        w = mof(98, 80, kind=inputs.SHAPE_OCTAHEDRON, rot_seed=9)
+    else:
+        w = mof(64, 10)
+        w.shape = inputs.Shape(inputs.SHAPE_ALL)
+    want = oracle_density(w, out_dtype=dtype)
+    rng = torch.tensor([2 ** 31 - 1, -1], dtype=torch.int32, device="cuda")
+    got = api.build_density(w.n, dev(w.cell), w.shape, origin=w.origin, out_dtype=dtype, nz_range=rng)
+    torch.cuda.synchronize()
+    g = got.cpu().numpy()
+    assert g.tobytes() == want.tobytes()
+    lo, hi = density.nonzero_plane_range(want)
+    assert rng.cpu().tolist() == [lo, hi]
+
+
+def test_density_weights_and_plane_subrange():
+    w = mof(64, 40)
+    weights = np.random.default_rng(3).random((64, 64, 64)).astype(np.float32)
+    w.shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
+    want = oracle_density(w, z_begin=9, z_count=23, weights=weights)
+    got = api.build_density(64, dev(w.cell), w.shape, weights=dev(weights), z_begin=9, z_count=23)
+    assert got.cpu().numpy().tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("f,n_out,src_dtype,out_dtype", [(4, 32, "f16", "f16"), (16, 16, "f16", "f16"),
+                                                          (2, 48, "f16", "f32"), (4, 20, "f32", "f32")])
+def test_zoom_block_sums(f, n_out, src_dtype, out_dtype):
+    w = mof(64, 50)
+    ed1 = oracle_density(w, out_dtype=src_dtype)
+    want = density.zoom_out(ed1, f, n_out, out_dtype=out_dtype)
+    got = api.zoom_density(dev(ed1), f, n_out, out_dtype=out_dtype).cpu().numpy()
+    if src_dtype == "f16":
+        assert got.tobytes() == want.tobytes()
+    else:  # float64 sums in another order, one rounding to float32
+        assert np.allclose(got, want, rtol=2 ** -23, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Forward: transform, |F|^2, Q bins
+# ---------------------------------------------------------------------------
+def gpu_forward(w, rho, F=False, dtype="f32"):
+    z0, nz = z_range(rho) if np.any(rho) else (0, 1)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz, ed_dtype=dtype)
+    ed = dev(rho[z0:z0 + nz])
+    Fo = torch.empty((w.n, w.n, w.n // 2 + 1, 2), dtype=torch.float32, device="cuda") if F else None
+    bins = api.fft_intensity(plan, ed, F_out=Fo)
+    torch.cuda.synchronize()
+    return plan, bins.cpu().numpy(), (Fo.cpu().numpy() if F else None)
+
+
+@pytest.mark.parametrize("case", ["sc64", "mof96", "mof98", "mof100", "mof120_cube", "mof128_small", "mof160"])
+def test_forward_bins_match_oracle(case):
+    if case == "sc64":
+        w = inputs.sc64_workload()
+    elif case == "mof120_cube":
+        w = mof(120, 56, kind=inputs.SHAPE_CUBE, rot_seed=2)
+    elif case == "mof128_small":
+        w = mof(128, 11)
+    else:
+        n = int(case[3:])
+        w = mof(n, int(n * 0.45))
+    rho = oracle_density(w)
+    _, gb, _ = gpu_forward(w, rho)
+    ob = oracle_forward(rho, w.dx, w.edges)
+    rep = compare_bins(gb, ob, rho.astype(np.float64), case)
+    print(case, rep)
+
+
+def test_forward_full_box_single_plane_and_zero_density():
+    w = mof(64, 30)
+    rho = oracle_density(w)
+    # the whole box as the slab (no skipped planes)
+    plan = api.Plan(64, w.dx, w.edges, z0=0, nz=64)
+    gb = api.fft_intensity(plan, dev(rho)).cpu().numpy()
+    compare_bins(gb, oracle_forward(rho, w.dx, w.edges), rho.astype(np.float64), "full box")
+    # a single nonzero plane
+    one = np.zeros_like(rho)
+    one[17] = rho[32]
+    plan = api.Plan(64, w.dx, w.edges, z0=17, nz=1)
+    gb = api.fft_intensity(plan, dev(one[17:18])).cpu().numpy()
+    compare_bins(gb, oracle_forward(one, w.dx, w.edges), one.astype(np.float64), "one plane")
+    # zero density: zero means, exact counts
+    zero = np.zeros((5, 64, 64), dtype=np.float32)
+    plan = api.Plan(64, w.dx, w.edges, z0=30, nz=5)
+    gb = api.fft_intensity(plan, dev(zero)).cpu().numpy()
+    ob = oracle_forward(np.zeros((64, 64, 64)), w.dx, w.edges)
+    assert np.array_equal(gb[0].astype(np.int64), ob["count"])
+    nz = ob["count"] > 0
+    assert np.all(gb[4][nz] == 0.0) and np.all(gb[1] == 0.0)
+
+
+def test_F_out_matches_eq1():
+    w = mof(96, 44)
+    rho = oracle_density(w)
+    _, _, F = gpu_forward(w, rho, F=True)
+    Fo = scatter.dft3(rho)[:, :, : w.n // 2 + 1]
+    Fg = F[..., 0] + 1j * F[..., 1]
+    err = np.abs(Fg - Fo).max() / np.abs(Fo).max()
+    assert err < 2e-6, err
+
+
+def test_fp16_ed_forward():
+    w = mof(128, 60)
+    rho16 = oracle_density(w, out_dtype="f16")
+    z0, nz = z_range(rho16)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz, ed_dtype="f16")
+    gb = api.fft_intensity(plan, dev(rho16[z0:z0 + nz])).cpu().numpy()
+    r64 = rho16.astype(np.float64)
+    compare_bins(gb, oracle_forward(r64, w.dx, w.edges), r64, "fp16 ED")
+
+
+def test_plan_thresholds_equal_host_table():
+    w = inputs.sc64_workload()
+    plan = api.Plan(w.n, w.dx, w.edges)
+    assert np.array_equal(plan.thresholds(), api.bin_thresholds(w.n, w.dx, w.edges))
+
+
+def test_bin_q_standalone():
+    w = mof(64, 30, nbins=40)
+    rho = oracle_density(w)
+    ob = oracle_forward(rho, w.dx, w.edges)
+    Ihalf = ob["I"][:, :, : w.n // 2 + 1].astype(np.float32)
+    plan = api.Plan(w.n, w.dx, w.edges)
+    gb = api.bin_q(plan, dev(Ihalf)).cpu().numpy()
+    # the same float32 intensities binned by the oracle (mirrored voxels may differ by one ulp)
+    ob32 = scatter.bin_intensity(ob["I"].astype(np.float32).astype(np.float64), w.n, w.dx, w.edges)
+    assert np.array_equal(gb[0].astype(np.int64), ob32["count"])
+    nz = ob32["count"] > 0
+    assert np.allclose(gb[4][nz], ob32["mean"][nz], rtol=1e-6, atol=0)
+
+
+def test_merge_matches_oracle():
+    edges = inputs.log_edges(0.05, 20.0, 60)
+    levels = []
+    rng = np.random.default_rng(1)
+    for n, dx in [(32, 0.4), (32, 0.8), (64, 0.1)]:
+        cnt = rng.integers(0, 50, 60).astype(np.int64)
+        mean = rng.random(60)
+        sem = rng.random(60) * 0.1
+        mq = rng.random(60) * 10
+        levels.append({"n": n, "dx": dx, "count": cnt, "mean": np.where(cnt > 0, mean, np.nan), "sem": sem, "mean_q": mq})
+    want = omerge.merge_levels(levels, edges)
+    dev_bins = []
+    for lv in levels:
+        b = np.zeros((6, 60))
+        b[0] = lv["count"]
+        b[3] = lv["mean_q"] * lv["count"]
+        b[4] = lv["mean"]
+        b[5] = lv["sem"]
+        dev_bins.append(dev(b))
+    out = api.merge(dev_bins, [lv["n"] for lv in levels], [math.pi / lv["dx"] for lv in levels], dev(edges))
+    o = out.cpu().numpy()
+    assert np.array_equal(o[4].astype(np.int64), want["source"])
+    assert np.array_equal(o[2].astype(np.int64), want["count"])
+    ok = want["source"] >= 0
+    assert np.array_equal(o[0][ok], want["mean"][ok])
+    assert np.array_equal(o[1][ok], want["sem"][ok])
+    assert np.allclose(o[3][ok], want["mean_q"][ok], rtol=1e-15)
+    assert np.all(np.isnan(o[0][~ok]))
+
+
+# ---------------------------------------------------------------------------
+# Adjoint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["recompute", "F_given", "weights_origin"])
+def test_backward_matches_oracle_gradient(mode):
+    if mode == "weights_origin":
+        w = mof(64, 40, ucell=16, a_nm=0.65, origin=(2, 7, 5))
+        weights = np.random.default_rng(4).random((64, 64, 64)).astype(np.float32)
+        weights[:10] = 0
+        weights[54:] = 0
+        w.shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
+    else:
+        w = inputs.sc64_workload()
+        weights = None
+    rho = oracle_density(w, weights=weights)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    Fo = torch.empty((w.n, w.n, w.n // 2 + 1, 2), device="cuda") if mode == "F_given" else None
+    bins = api.fft_intensity(plan, dev(rho[z0:z0 + nz]), ws=ws, F_out=Fo)
+    # loss: log-MSE against the closed-form sphere curve of the same electron count
+    gb = bins.cpu().numpy()
+    ne = float(rho.astype(np.float64).sum())
+    target = inputs.sphere_target_curve(gb[3] / np.maximum(gb[0], 1), 1.0, ne) / w.n ** 6 + 1e-30
+    L, g = adjoint.loss_log_mse(gb[4], target)
+    dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws, origin=w.origin,
+                                weights=dev(weights) if weights is not None else None, F=Fo)
+    torch.cuda.synchronize()
+    mask = density.mask_values(w.n, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot, weights)
+    ob_count = oracle_forward(rho, w.dx, w.edges)["count"]
+    gu, gm = oracle_grads(rho.astype(np.float64), w.cell.astype(np.float64), mask, w.dx, w.edges, g, ob_count,
+                          w.origin)
+    eu = normwise(dcell.cpu().numpy(), gu)
+    em = normwise(dmask.cpu().numpy(), gm)
+    print(mode, "dL/du", eu, "dL/dm", em)
+    assert eu <= GRAD_RTOL and em <= GRAD_RTOL
