@@ -3,9 +3,10 @@
 Workload (one step): the 512^3 FP32 grid of a 2.6 nm MOF-like cell (60
 Gaussian atoms, 64^3 samples, seed 0) tiled and cut by a 10 nm sphere, 512
 log-spaced Q bins from dq to pi/dx:
-  ur_build_density (the 247 nonzero planes) -> ur_fft_intensity (plane pass,
-  column pass with fused |F|^2 and binning) -> dL/d(mean I) of a log-MSE loss
-  against the closed-form sphere curve -> ur_backward (dL/d cell, dL/d mask).
+  ur_fft_intensity_tiled (the density of the 247 nonzero planes generated
+  inside the plane pass, column pass with fused |F|^2 and binning) ->
+  dL/d(mean I) of a log-MSE loss against the closed-form sphere curve ->
+  ur_backward (dL/d cell, dL/d mask).
 All inputs are synthetic and larger than L2 (ED slab 259 MB, intermediate
 520 MB), so no explicit L2 flush is done between steps.
 
@@ -115,7 +116,7 @@ def kernel_bytes(n: int, P: int, U: int):
     Y = 8 * n * n * H           # adjoint intermediate, all planes
     return {
         "density": 4 * n * n * P,
-        "rows_r2c": 4 * n * n * P + X,
+        "rows_r2c": X,          # density generated in the kernel: only the intermediate is written
         "cols_y": 2 * X,
         "cols_z_bin": X,
         "finalize": 0,
@@ -171,8 +172,7 @@ def run_ours(args):
     target = torch.from_numpy(inputs.sphere_target_curve(qm, radius, ne) / float(n) ** 6 + 1e-300).cuda()
 
     def step():
-        api.build_density(n, cell, w.shape, z_begin=z0, z_count=P, out=ed)
-        api.fft_intensity(plan, ed, bins=bins, ws=ws)
+        api.fft_intensity_tiled(plan, cell, w.shape, bins=bins, ws=ws)
         mean = bins[api.BIN_MEAN]
         ok = torch.isfinite(mean) & (mean > 0)
         d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)
@@ -214,18 +214,23 @@ def run_ours(args):
         s = per.setdefault(name, [0.0, 0])
         s[0] += ms
         s[1] += 1
+    # kernel_bytes() is per step; a kernel launched in plane chunks moves that over
+    # launches/steps launches, so bytes per launch = per-step bytes * steps / launches.
     kb = kernel_bytes(n, P, w.ucell)
     dom = max(per.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_cnt) = dom
     hbm, src = peaks()
     avg_ms = dom_ms / dom_cnt
-    achieved = kb.get(dom_name, 0) / (avg_ms * 1e-3) / 1e9
+    bytes_per_launch = kb.get(dom_name, 0) * args.steps / dom_cnt
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     kernels = {k: {"launches": c, "avg_us": 1e3 * ms / c, "share": ms / sum(v[0] for v in per.values()),
-                   "gbs": (kb.get(k, 0) / (ms / c * 1e-3) / 1e9) if kb.get(k, 0) else None}
+                   "bytes_per_launch": kb.get(k, 0) * args.steps / c,
+                   "gbs": (kb.get(k, 0) * args.steps / (ms * 1e-3) / 1e9) if kb.get(k, 0) else None}
                for k, (ms, c) in per.items()}
-    # step-level algorithmic bytes: forward 4 N^2 P + 16 N H P (two-pass minimum) + adjoint
+    # step-level algorithmic bytes: forward 16 N H P (intermediate written and read once; the
+    # density is generated, not read) + adjoint
     H = n // 2 + 1
-    fwd_alg = 4 * n * n * P + 16 * n * H * P
+    fwd_alg = 16 * n * H * P
     adj_alg = 8 * n * H * P + 24 * n * n * H + 4 * n ** 3
     step_frac = (fwd_alg + adj_alg) / (ms_step * 1e-3) / 1e9 / hbm
 
@@ -238,8 +243,7 @@ def run_ours(args):
 
     def e2e_step():
         cell_dev.copy_(cell_host, non_blocking=True)
-        api.build_density(n, cell_dev, w.shape, z_begin=z0, z_count=P, out=ed)
-        api.fft_intensity(plan, ed, bins=bins, ws=ws)
+        api.fft_intensity_tiled(plan, cell_dev, w.shape, bins=bins, ws=ws)
         mean = bins[api.BIN_MEAN]
         ok = torch.isfinite(mean) & (mean > 0)
         d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)

@@ -169,6 +169,15 @@ ur_status ur_zoom_density(int32_t n_src, int32_t src_dtype, const void* src, int
 ur_status ur_fft_intensity(const ur_plan* plan, const void* ed, int32_t ed_on_host, double* bins,
                            void* F_out, void* ws, size_t ws_bytes, void* stream);
 
+/* ur_fft_intensity with the density generated inside the plane pass
+ * (Sec. 2.3 tile + mask fused with Sec. 2.4): the ED of planes
+ * [z0, z0+nz) is never stored.  cell, ucell, origin, shape and weights are
+ * as for ur_build_density; the transform sees exactly the values
+ * ur_build_density would write (FP32).  The plan's ed_dtype is ignored. */
+ur_status ur_fft_intensity_tiled(const ur_plan* plan, const float* cell, int32_t ucell, const int32_t* origin,
+                                 const ur_shape* shape, const float* weights, double* bins, void* F_out, void* ws,
+                                 size_t ws_bytes, void* stream);
+
 /* Sec. 2.5 binning of a stored half-spectrum intensity I[kz][ky][kx]
  * (device float32, N*N*(N/2+1), Eq. 1 normalised); kx in (0, N/2) weighs 2
  * (the mirrored half), kx = 0 and N/2 weigh 1.  ws: ur_workspace_size(plan, UR_WS_FORWARD). */

@@ -48,6 +48,8 @@ SIGNATURES = {
                                 _vp, _vp, _vp]),
     "ur_zoom_density": (_i32, [_i32, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),
     "ur_fft_intensity": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "ur_fft_intensity_tiled": (_i32, [_vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp, _vp,
+                                      _sz, _vp]),
     "ur_bin_q": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _vp, _vp]),
     "ur_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
@@ -216,6 +218,22 @@ def fft_intensity(plan: Plan, ed: torch.Tensor, bins: torch.Tensor | None = None
         bins = new_bins(plan)
     _check("ur_fft_intensity", lib().ur_fft_intensity(plan.handle, _ptr(ed), on_host, _ptr(bins), _ptr(F_out), _ptr(ws),
                                                       ws.numel(), _stream(stream)))
+    return bins
+
+
+def fft_intensity_tiled(plan: Plan, cell: torch.Tensor, shape, origin=(0, 0, 0), weights: torch.Tensor | None = None,
+                        bins: torch.Tensor | None = None, F_out: torch.Tensor | None = None,
+                        ws: torch.Tensor | None = None, stream=None, want_bins: bool = True):
+    """Sec. 2.3 + 2.4 + 2.5 fused: density generated inside the plane pass, never stored."""
+    if ws is None:
+        ws = plan.workspace(UR_WS_FORWARD)
+    if bins is None and want_bins:
+        bins = new_bins(plan)
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
+    sd = shape_desc(shape)
+    _check("ur_fft_intensity_tiled", lib().ur_fft_intensity_tiled(plan.handle, _ptr(cell), cell.shape[0], org,
+                                                                  C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
+                                                                  _ptr(ws), ws.numel(), _stream(stream)))
     return bins
 
 

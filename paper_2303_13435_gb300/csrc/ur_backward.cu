@@ -19,30 +19,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "ur_forward.cuh"
-
-struct GradShape {
-  int kind;
-  float cx, cy, cz, s;
-  float r[9];
-};
-
-__device__ __forceinline__ float grad_mask_at(const GradShape& sh, int x, int y, int z) {
-  if (sh.kind == UR_SHAPE_ALL) return 1.f;
-  const float dx = __fsub_rn((float)x, sh.cx);
-  const float dy = __fsub_rn((float)y, sh.cy);
-  const float dz = __fsub_rn((float)z, sh.cz);
-  if (sh.kind == UR_SHAPE_SPHERE) {
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    return d2 <= __fmul_rn(sh.s, sh.s) ? 1.f : 0.f;
-  }
-  float p[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    p[a] = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(sh.r[a], dx), __fmul_rn(sh.r[3 + a], dy)), __fmul_rn(sh.r[6 + a], dz)));
-  if (sh.kind == UR_SHAPE_CUBE) return (p[0] <= sh.s && p[1] <= sh.s && p[2] <= sh.s) ? 1.f : 0.f;
-  return __fadd_rn(__fadd_rn(p[0], p[1]), p[2]) <= sh.s ? 1.f : 0.f;
-}
+#include "ur_fast.cuh"
 
 // sigma_j = 2 g_j / (n_j N^3) (scale of F~), or 2 g_j / n_j when F (= F~/N^3) is read
 __global__ void k_sigma(const double* __restrict__ g, const double* __restrict__ fwd_bins, int nb, double n3, int f_given,
@@ -62,7 +39,7 @@ __global__ void k_sigma(const double* __restrict__ g, const double* __restrict__
 __global__ void __launch_bounds__(256, 2) k_rows_grad(const float2* __restrict__ Y, int N, int RB,
                                                    const StageInfo* __restrict__ sched, int nst,
                                                    const float2* __restrict__ tw, const float* __restrict__ cell, int U,
-                                                   int ox, int oy, int oz, GradShape sh, const float* __restrict__ weights,
+                                                   int ox, int oy, int oz, ShapeArgs sh, const float* __restrict__ weights,
                                                    float inv_n3, float* __restrict__ dl_dmask, float* __restrict__ dl_dcell) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int M = N >> 1, H = M + 1;
@@ -144,8 +121,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_grad(const float2* __restrict__
         m0 = wv.x;
         m1 = wv.y;
       } else {
-        m0 = grad_mask_at(sh, x0, y, z);
-        m1 = grad_mask_at(sh, x0 + 1, y, z);
+        m0 = mask_at(sh, x0, y, z);
+        m1 = mask_at(sh, x0 + 1, y, z);
       }
       if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
       if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
@@ -202,8 +179,59 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
   }
   const long long tiles = (a.ncols + a.TX - 1) / a.TX;
   ur_timing_begin("adj_cols_z", s);
-  UR_TRY(ur_launch_cols(COL_ZADJ, false, p, a, (int)tiles, p->col_smem, s));
+  if (p->fast) {
+    UR_TRY(ur_fast_cols(n, 3 /* z adjoint */, a, s));
+  } else {
+    UR_TRY(ur_launch_cols(COL_ZADJ, false, p, a, (int)tiles, p->col_smem, s));
+  }
   ur_timing_end(s);
+
+  if (p->fast) {
+    // B2 + B3 in plane chunks: the y-inverse of a chunk goes to a chunk buffer
+    // that stays in L2 until the row pass of the same chunk has read it.
+    UR_REQUIRE(!weights || ((uintptr_t)weights % 8) == 0, "ur_backward: weights must be 8-byte aligned");
+    float2* C = (float2*)((char*)sigma + ur_align_up(p->ws_sigma, 256));
+    GradArgs g;
+    memset(&g, 0, sizeof g);
+    g.tw = p->tw;
+    g.cell = cell;
+    g.ucell = ucell;
+    if (origin) {
+      g.ox = origin[0];
+      g.oy = origin[1];
+      g.oz = origin[2];
+    }
+    g.sh = ur_shape_args(shape);
+    g.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;
+    g.inv_n3 = (float)(1.0 / n3);
+    g.dl_dmask = dl_dmask;
+    g.dl_dcell = dl_dcell;
+    UR_CUDA_CHECK(cudaMemsetAsync(dl_dcell, 0, sizeof(float) * (size_t)ucell * ucell * ucell, s));
+    for (int p0 = 0; p0 < n; p0 += p->chunk_planes) {
+      const int np = (p0 + p->chunk_planes <= n) ? p->chunk_planes : n - p0;
+      ColArgs b = ur_col_args(p);
+      b.src = Y + (long long)p0 * n * H;
+      b.dst = C;
+      b.ncols = (long long)np * H;
+      b.A = (long long)n * H;
+      b.S = H;
+      b.Ad = b.A;
+      b.Sd = b.S;
+      b.nload = n;
+      b.zoff = 0;
+      b.nbins = 0;
+      ur_timing_begin("adj_cols_y", s);
+      UR_TRY(ur_fast_cols(n, 1 /* y inverse */, b, s));
+      ur_timing_end(s);
+      g.Y = C;
+      g.ybase_z = p0;
+      g.z0 = p0;
+      ur_timing_begin("adj_rows_grad", s);
+      UR_TRY(ur_fast_rows_grad(n, g, np, s));
+      ur_timing_end(s);
+    }
+    return UR_OK;
+  }
 
   // B2
   ColArgs b = ur_col_args(p);
@@ -222,13 +250,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
   ur_timing_end(s);
 
   // B3
-  GradShape sh;
-  sh.kind = shape->kind;
-  sh.cx = shape->center[0];
-  sh.cy = shape->center[1];
-  sh.cz = shape->center[2];
-  sh.s = shape->size;
-  memcpy(sh.r, shape->rot, sizeof sh.r);
+  const ShapeArgs sh = ur_shape_args(shape);
   int ox = 0, oy = 0, oz = 0;
   if (origin) {
     ox = origin[0];

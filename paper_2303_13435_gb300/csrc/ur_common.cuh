@@ -370,6 +370,7 @@ struct ur_plan {
   int device, num_sms;
   float2* tw;        // device [n]
   int32_t* thr;      // device [nbins+1]
+  int16_t* binlut;   // device [3 (N/2)^2 + 1]: bin of k^2 = s, -1 outside every bin
   int64_t* thr_host; // host   [nbins+1]
   double* geo;       // device [2][nbins]: count, sum |Q|
   Sched sched_n, sched_m;       // host copies
@@ -385,6 +386,10 @@ struct ur_plan {
   size_t ws_sigma;   // nbins floats (+pad)
   size_t ws_slab;    // one host-staging slab
   int slab_planes;
+  // power-of-two path
+  int fast;          // 1: compile-time kernels (N a power of two in [64, 1024])
+  int chunk_planes;  // planes per L2-resident chunk of the plane pass / adjoint rows
+  size_t ws_chunk;   // adjoint chunk buffer
 };
 
 // kernels launched from host code in other translation units

@@ -11,31 +11,7 @@
 #include <type_traits>
 
 #include "ur_forward.cuh"
-
-struct ShapeArgs {
-  int kind;
-  float cx, cy, cz, s;
-  float r[9];
-};
-
-// Mask value at voxel (x, y, z): every product and sum rounded separately
-// (no contraction), in the order of the ur_build_density contract.
-__device__ __forceinline__ float mask_at(const ShapeArgs& sh, int x, int y, int z) {
-  if (sh.kind == UR_SHAPE_ALL) return 1.f;
-  const float dx = __fsub_rn((float)x, sh.cx);
-  const float dy = __fsub_rn((float)y, sh.cy);
-  const float dz = __fsub_rn((float)z, sh.cz);
-  if (sh.kind == UR_SHAPE_SPHERE) {
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    return d2 <= __fmul_rn(sh.s, sh.s) ? 1.f : 0.f;
-  }
-  float p[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    p[a] = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(sh.r[a], dx), __fmul_rn(sh.r[3 + a], dy)), __fmul_rn(sh.r[6 + a], dz)));
-  if (sh.kind == UR_SHAPE_CUBE) return (p[0] <= sh.s && p[1] <= sh.s && p[2] <= sh.s) ? 1.f : 0.f;
-  return __fadd_rn(__fadd_rn(p[0], p[1]), p[2]) <= sh.s ? 1.f : 0.f;  // octahedron
-}
+#include "ur_density.cuh"
 
 template <typename T>
 __device__ __forceinline__ void store2(T* out, float a, float b);
@@ -87,12 +63,7 @@ static ur_status shape_args(const ur_shape* shape, ShapeArgs* sh) {
   UR_REQUIRE(shape, "ur_build_density: null shape");
   UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_build_density: bad shape kind %d",
              shape->kind);
-  sh->kind = shape->kind;
-  sh->cx = shape->center[0];
-  sh->cy = shape->center[1];
-  sh->cz = shape->center[2];
-  sh->s = shape->size;
-  memcpy(sh->r, shape->rot, sizeof sh->r);
+  *sh = ur_shape_args(shape);
   return UR_OK;
 }
 

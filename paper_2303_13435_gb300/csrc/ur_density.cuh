@@ -1,0 +1,78 @@
+// Particle-mask predicate and unit-cell lookup shared by the density kernel,
+// the fused density + transform row pass and the adjoint row pass (Sec. 2.3).
+#pragma once
+
+#include "ur_common.cuh"
+
+struct ShapeArgs {
+  int kind;
+  float cx, cy, cz, s;
+  float r[9];
+};
+
+// Mask value at voxel (x, y, z): every product and sum rounded separately
+// (no contraction), in the order of the ur_build_density contract.
+__device__ __forceinline__ float mask_at(const ShapeArgs& sh, int x, int y, int z) {
+  if (sh.kind == UR_SHAPE_ALL) return 1.f;
+  const float dx = __fsub_rn((float)x, sh.cx);
+  const float dy = __fsub_rn((float)y, sh.cy);
+  const float dz = __fsub_rn((float)z, sh.cz);
+  if (sh.kind == UR_SHAPE_SPHERE) {
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return d2 <= __fmul_rn(sh.s, sh.s) ? 1.f : 0.f;
+  }
+  float p[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    p[a] = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(sh.r[a], dx), __fmul_rn(sh.r[3 + a], dy)), __fmul_rn(sh.r[6 + a], dz)));
+  if (sh.kind == UR_SHAPE_CUBE) return (p[0] <= sh.s && p[1] <= sh.s && p[2] <= sh.s) ? 1.f : 0.f;
+  return __fadd_rn(__fadd_rn(p[0], p[1]), p[2]) <= sh.s ? 1.f : 0.f;  // octahedron
+}
+
+// Per-row part of the predicate: the y and z terms are fixed along a row, so
+// they are formed once (with the same roundings) and only the x term varies.
+struct RowMask {
+  int kind;
+  float s, s2, dyz2;   // sphere: fl(dy*dy) and fl(dz*dz) folded below
+  float dy2, dz2;
+  float cx;
+  float ry[3], rz[3];  // fl(R[1][a] dy), fl(R[2][a] dz)
+  float r0[3];
+  __device__ __forceinline__ void init(const ShapeArgs& sh, int y, int z) {
+    kind = sh.kind;
+    s = sh.s;
+    s2 = __fmul_rn(sh.s, sh.s);
+    cx = sh.cx;
+    const float dy = __fsub_rn((float)y, sh.cy);
+    const float dz = __fsub_rn((float)z, sh.cz);
+    dy2 = __fmul_rn(dy, dy);
+    dz2 = __fmul_rn(dz, dz);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r0[a] = sh.r[a];
+      ry[a] = __fmul_rn(sh.r[3 + a], dy);
+      rz[a] = __fmul_rn(sh.r[6 + a], dz);
+    }
+  }
+  __device__ __forceinline__ float at(int x) const {
+    if (kind == UR_SHAPE_ALL) return 1.f;
+    const float dx = __fsub_rn((float)x, cx);
+    if (kind == UR_SHAPE_SPHERE) return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), dy2), dz2) <= s2 ? 1.f : 0.f;
+    float p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(r0[a], dx), ry[a]), rz[a]));
+    if (kind == UR_SHAPE_CUBE) return (p[0] <= s && p[1] <= s && p[2] <= s) ? 1.f : 0.f;
+    return __fadd_rn(__fadd_rn(p[0], p[1]), p[2]) <= s ? 1.f : 0.f;
+  }
+};
+
+static inline ShapeArgs ur_shape_args(const ur_shape* shape) {
+  ShapeArgs sh;
+  sh.kind = shape->kind;
+  sh.cx = shape->center[0];
+  sh.cy = shape->center[1];
+  sh.cz = shape->center[2];
+  sh.s = shape->size;
+  for (int i = 0; i < 9; ++i) sh.r[i] = shape->rot[i];
+  return sh;
+}

@@ -1,0 +1,501 @@
+// Power-of-two grid edges (64 <= N <= 1024): compile-time transforms.
+//
+// A length-L line is held by L/8 threads, eight complex values each
+// (thread j holds positions j + q L/8, q = 0..7).  Each Stockham stage is a
+// radix-8 butterfly in registers (the last stage radix 4 or 2 when log2 L is
+// not a multiple of 3); between stages the values cross shared memory once,
+// at padded addresses i + i/16 so that neither the strided writes nor the
+// contiguous reads conflict in banks.  After the last stage a thread again
+// holds positions j + q L/8, so the first stage can read and the last stage
+// can write global memory directly.
+//
+// Kernels (Sec. 2.4 Eq. 2 split, Sec. 2.5 binning, and the adjoint):
+//   k_p2_rows<N, GEN>  rows along x: real-to-complex via an N/2-point
+//                      transform; GEN = 1 generates the density of the row
+//                      on the fly (Sec. 2.3 tile + mask) instead of reading ED
+//   k_p2_cols<N, MODE> columns along y (in place or into another buffer,
+//                      forward or inverse) or along z (+ |F|^2 binning, or the
+//                      adjoint's scale-and-invert)
+//   k_p2_rows_grad<N>  inverse real transform along x + dL/dm, dL/du
+#include <math.h>
+#include <string.h>
+
+#include "ur_density.cuh"
+#include "ur_fast.cuh"
+
+#define BIN_CHUNK_F 8
+
+template <int L>
+struct P2 {
+  static constexpr int LOG = L == 8 ? 3 : L == 16 ? 4 : L == 32 ? 5 : L == 64 ? 6 : L == 128 ? 7 : L == 256 ? 8
+                                                                                           : L == 512 ? 9 : L == 1024 ? 10 : 11;
+  static constexpr int T = L / 8;
+  static constexpr int NFULL = LOG / 3;
+  static constexpr int REM = LOG % 3;
+  static constexpr int NST = NFULL + (REM ? 1 : 0);
+  static constexpr int PITCH = L + L / 16;
+};
+
+__device__ __forceinline__ int p2pad(int i) { return i + (i >> 4); }
+
+constexpr int ipow8(int s) { return s == 0 ? 1 : 8 * ipow8(s - 1); }
+
+// Butterflies of one stage.  Thread j runs 8/R butterflies b = j + i L/8; the
+// inputs of butterfly i are v[i + (8/R) r], r < R; k = b mod NS; twiddle
+// exp(-+2 pi i r k/(NS R)) read from a table of exp(-2 pi i t/(L tws)).
+template <int L, int R, int NS, bool INV>
+__device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const float2* __restrict__ tw, int tws) {
+  constexpr int T = L / 8, NB = 8 / R;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = j + i * T;
+    const int k = b & (NS - 1);
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = v[i + NB * r];
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) a[r] = twmul<INV>(a[r], __ldg(tw + (r * k * (L / (NS * R))) * tws));
+    }
+    dft<R, INV>(a);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i + NB * r] = a[r];
+  }
+}
+
+// Stage outputs to shared memory at (b - k) R + k + r NS, then reload as j + q L/8.
+template <int L, int R, int NS>
+__device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line) {
+  constexpr int T = L / 8, NB = 8 / R;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = j + i * T;
+    const int k = b & (NS - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) line[p2pad((b - k) * R + k + r * NS)] = v[i + NB * r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = line[p2pad(j + q * T)];
+  __syncthreads();
+}
+
+template <int L, bool INV, int S>
+struct P2Run {
+  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws) {
+    constexpr int NST = P2<L>::NST, NFULL = P2<L>::NFULL, REM = P2<L>::REM;
+    if constexpr (S < NST) {
+      constexpr int R = (S < NFULL) ? 8 : (1 << REM);
+      constexpr int NS = ipow8(S);
+      p2_butterflies<L, R, NS, INV>(v, j, tw, tws);
+      if constexpr (S + 1 < NST) p2_exchange<L, R, NS>(v, j, line);
+      P2Run<L, INV, S + 1>::run(v, j, line, tw, tws);
+    }
+  }
+};
+
+// Whole line transform; every thread of the block must call it (it synchronises).
+template <int L, bool INV>
+__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws) {
+  P2Run<L, INV, 0>::run(v, j, line, tw, tws);
+}
+
+// ---------------------------------------------------------------------------
+// Rows: real-to-complex along x (pass 1a), optionally generating the density.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float2 ld_pair(const T* p);
+template <>
+__device__ __forceinline__ float2 ld_pair<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+template <>
+__device__ __forceinline__ float2 ld_pair<__half>(const __half* p) {
+  return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+}
+
+template <int N, int GEN, typename TED>
+__global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
+  constexpr int M = N / 2, H = M + 1, T = M / 8, RB = 512 / T, PITCH = P2<M>::PITCH;
+  __shared__ __align__(16) float2 sm[RB * PITCH];
+  const int t = threadIdx.x / T, j = threadIdx.x - (threadIdx.x / T) * T;
+  const long long r = (long long)blockIdx.x * RB + t;
+  const bool valid = r < a.nrows;
+  float2* line = sm + t * PITCH;
+  float2 v[8];
+  if (GEN) {
+    const int p = (int)(r / N), y = (int)(r - (long long)p * N);
+    const int z = a.z0 + p;
+    RowMask rm;
+    rm.init(a.sh, y, z);
+    const int U = a.ucell;
+    const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
+    const float* wrow = a.weights ? a.weights + ((long long)z * N + y) * N : nullptr;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = 2 * (j + q * T);
+      float e0 = 0.f, e1 = 0.f;
+      if (valid) {
+        const int c0 = (x + a.ox) % U, c1 = (x + 1 + a.ox) % U;
+        float m0, m1;
+        if (wrow) {
+          const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+          m0 = mw.x;
+          m1 = mw.y;
+        } else {
+          m0 = rm.at(x);
+          m1 = rm.at(x + 1);
+        }
+        e0 = __fmul_rn(__ldg(crow + c0), m0);
+        e1 = __fmul_rn(__ldg(crow + c1), m1);
+      }
+      v[q] = make_float2(e0, e1);
+    }
+  } else {
+    const TED* row = reinterpret_cast<const TED*>(a.ed) + r * N;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = valid ? ld_pair<TED>(row + 2 * (j + q * T)) : make_float2(0.f, 0.f);
+  }
+  p2_fft<M, false>(v, j, line, a.tw, 2);
+  // split step: X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2
+#pragma unroll
+  for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
+  __syncthreads();
+  if (valid) {
+    float2* X = a.X + r * H;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      int k = j + q * T;
+      if (q == 8) {
+        if (j != 0) break;
+        k = M;
+      }
+      const float2 zk = line[p2pad(k == M ? 0 : k)];
+      const float2 zc = cconj(line[p2pad(k == 0 ? 0 : M - k)]);
+      const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+      const float2 d = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
+      const float2 o = make_float2(d.y, -d.x);
+      X[k] = cadd(e, cmul(__ldg(a.tw + k), o));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Columns.  Block = TX columns x L/8 threads; thread (j, c), c fastest, so a
+// warp reads whole row segments of TX consecutive columns.
+// ---------------------------------------------------------------------------
+enum { P2_Y_FWD = 0, P2_Y_INV = 1, P2_Z_BIN = 2, P2_Z_ADJ = 3 };
+
+// bins of the 8 values of thread j (kz = j + qT), from the k^2 -> bin table
+template <int N>
+__device__ __forceinline__ void p2_bins8(int c2, int j, const int16_t* __restrict__ lut, int (&bin)[8]) {
+  constexpr int T = N / 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int kz = j + q * T;
+    const int m = kz <= N / 2 ? kz : N - kz;
+    bin[q] = __ldg(lut + c2 + m * m);
+  }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(512) k_p2_cols(ColArgs a) {
+  // column pitch = 2 (mod 16) float2: the TX columns a warp touches fall on different banks
+  constexpr int T = N / 8, TX = 512 / T, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_blo, s_bhi;
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  constexpr size_t BUF_BYTES = ((size_t)TX * PITCH * sizeof(float2) + 15) / 16 * 16;
+  int32_t* thr = reinterpret_cast<int32_t*>(smraw + BUF_BYTES);
+  float* hs = reinterpret_cast<float*>(smraw + BUF_BYTES + ur_align_up_dev((size_t)(a.nbins + 1) * 4, 16));
+  float* hs2 = hs + a.nbins;
+  const int c = threadIdx.x % TX, j = threadIdx.x / TX;
+  const int col0 = blockIdx.x * TX;
+  const int col = col0 + c;
+  const bool valid = col < a.ncols;
+  const bool binning = (MODE == P2_Z_BIN || MODE == P2_Z_ADJ) && a.nbins > 0;
+  if (MODE == P2_Z_BIN && binning) {
+    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
+    if (MODE == P2_Z_BIN && threadIdx.x == 0) {
+      s_blo = 0x7fffffff;
+      s_bhi = -1;
+    }
+    __syncthreads();
+  }
+  // column position of the spectrum (z passes): kx, ky
+  int kx = 0, ky = 0;
+  {
+    const int o = col / H;
+    kx = col - o * H;
+    ky = o < M ? o : o - N;
+  }
+  const int c2 = kx * kx + ky * ky;
+  if (MODE == P2_Z_BIN && binning) {
+    if (j == 0 && valid) {
+      atomicMin(&s_blo, max(bin_search(thr, a.nbins, c2), 0));
+      atomicMax(&s_bhi, min(bin_search(thr, a.nbins, c2 + M * M), a.nbins - 1));
+    }
+    __syncthreads();
+    for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
+      hs[i] = 0.f;
+      hs2[i] = 0.f;
+    }
+  }
+  const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int li = j + q * T - a.zoff;
+    v[q] = (valid && li >= 0 && li < a.nload) ? __ldg(a.src + sbase + (long long)li * a.S) : make_float2(0.f, 0.f);
+    if (a.fin_mul != 1.f) v[q] = cscale(v[q], a.fin_mul);
+  }
+  float2* line = buf + c * PITCH;
+  if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
+    p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.tw, 1);
+    if (valid) {
+      const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+    }
+  } else if (MODE == P2_Z_BIN) {
+    p2_fft<N, false>(v, j, line, a.tw, 1);
+    if (a.fout && valid) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a.fout[(long long)(j + q * T) * N * H + col] = cscale(v[q], a.fscale);
+    }
+    if (binning) {
+      // natural order in shared memory, then contiguous |kz| chunks per thread
+#pragma unroll
+      for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
+      __syncthreads();
+      constexpr int NCH = (H + BIN_CHUNK_F - 1) / BIN_CHUNK_F;
+      for (int task = threadIdx.x; task < TX * NCH; task += blockDim.x) {
+        const int tc = task % TX, ch = task / TX;
+        const int gcol = col0 + tc;
+        if (gcol >= a.ncols) continue;
+        const int o = gcol / H, kx2 = gcol - o * H, ky2 = o < M ? o : o - N;
+        const int cc2 = kx2 * kx2 + ky2 * ky2;
+        const float w = (kx2 == 0 || kx2 == M) ? 1.f : 2.f;
+        const float2* ln = buf + tc * PITCH;
+        const int m0 = ch * BIN_CHUNK_F, m1 = min(m0 + BIN_CHUNK_F, M + 1);
+        int run = __ldg(a.lut + cc2 + m0 * m0);
+        float sI = 0.f, sI2 = 0.f;
+        for (int m = m0; m < m1; ++m) {
+          const int cur = __ldg(a.lut + cc2 + m * m);
+          if (cur != run) {
+            if (run >= 0 && run < a.nbins) {
+              atomicAdd(hs + run, w * sI);
+              atomicAdd(hs2 + run, w * sI2);
+            }
+            run = cur;
+            sI = 0.f;
+            sI2 = 0.f;
+          }
+          const float2 f1 = ln[p2pad(m)];
+          const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
+          sI += i1;
+          sI2 += i1 * i1;
+          if (m != 0 && m != M) {
+            const float2 f2 = ln[p2pad(N - m)];
+            const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
+            sI += i2;
+            sI2 += i2 * i2;
+          }
+        }
+        if (run >= 0 && run < a.nbins) {
+          atomicAdd(hs + run, w * sI);
+          atomicAdd(hs2 + run, w * sI2);
+        }
+      }
+      __syncthreads();
+      for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
+        if (hs[i] != 0.f) atomicAdd(a.gsum + i, (double)hs[i]);
+        if (hs2[i] != 0.f) atomicAdd(a.gsum2 + i, (double)hs2[i]);
+      }
+    }
+  } else {  // P2_Z_ADJ
+    if (!a.skip_fwd) p2_fft<N, false>(v, j, line, a.tw, 1);
+    int bin[8];
+    p2_bins8<N>(c2, j, a.lut, bin);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float sg = (bin[q] >= 0 && bin[q] < a.nbins) ? __ldg(a.sigma + bin[q]) : 0.f;
+      v[q] = cscale(v[q], sg);
+    }
+    p2_fft<N, true>(v, j, line, a.tw, 1);
+    if (valid) {
+      const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint rows: inverse real transform along x, then dL/dm and dL/du.
+// Block = RB rows (z, y) that share the cell row (cz, cy): y = yf + U t.
+//   Z[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) conj(W_N^k),
+//   z = IFFT_{N/2}(Z),  (g(2m), g(2m+1)) = (Re z[m], Im z[m]).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
+  constexpr int M = N / 2, H = M + 1, T = M / 8, PITCH = P2<M>::PITCH + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int RB = a.rb;
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  float* acc = reinterpret_cast<float*>(smraw + ur_align_up_dev((size_t)RB * PITCH * sizeof(float2), 16));
+  const int U = a.ucell;
+  const int t = threadIdx.x / T, j = threadIdx.x - (threadIdx.x / T) * T;
+  const int cy = blockIdx.y;
+  const int z = a.z0 + blockIdx.z;
+  const int cz = (z + a.oz) % U;
+  const int yf = ((cy - a.oy) % U + U) % U;
+  const int y = yf + U * (blockIdx.x * RB + t);
+  const bool valid = y < N;
+  for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
+  float2* line = sm + t * PITCH;
+  const float2* Yrow = a.Y + ((long long)(z - a.ybase_z) * N + (valid ? y : 0)) * H;
+  for (int k = j; k < H; k += T) line[p2pad(k)] = valid ? __ldg(Yrow + k) : make_float2(0.f, 0.f);
+  __syncthreads();
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int k = j + q * T;
+    const float2 xa = line[p2pad(k)], xb = line[p2pad(M - k)];
+    const float2 w = __ldg(a.tw + k);
+    const float2 e = cadd(xa, cconj(xb));
+    const float2 d = csub(xa, cconj(xb));
+    const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);
+    v[q] = make_float2(e.x - o.y, e.y + o.x);
+  }
+  __syncthreads();
+  p2_fft<M, true>(v, j, line, a.tw, 2);
+  const float* crow = a.cell + ((long long)cz * U + cy) * U;
+  RowMask rm;
+  rm.init(a.sh, valid ? y : 0, z);
+  const float* wrow = a.weights ? a.weights + ((long long)z * N + (valid ? y : 0)) * N : nullptr;
+  if (valid) {
+    float* drow = a.dl_dmask ? a.dl_dmask + ((long long)z * N + y) * N : nullptr;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = 2 * (j + q * T);
+      const float g0 = v[q].x * a.inv_n3, g1 = v[q].y * a.inv_n3;
+      const int c0 = (x + a.ox) % U, c1 = (x + 1 + a.ox) % U;
+      if (drow) *reinterpret_cast<float2*>(drow + x) = make_float2(g0 * __ldg(crow + c0), g1 * __ldg(crow + c1));
+      float m0, m1;
+      if (wrow) {
+        const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+        m0 = mw.x;
+        m1 = mw.y;
+      } else {
+        m0 = rm.at(x);
+        m1 = rm.at(x + 1);
+      }
+      if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
+      if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < U; i += blockDim.x)
+    if (acc[i] != 0.f) atomicAdd(a.dl_dcell + ((long long)cz * U + cy) * U + i, acc[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Host dispatch
+// ---------------------------------------------------------------------------
+bool ur_fast_supported(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+
+template <int N>
+static size_t cols_smem(int nbins) {
+  constexpr int T = N / 8, TX = 512 / T, PITCH = P2<N>::PITCH + 2;
+  return ur_align_up((size_t)TX * PITCH * sizeof(float2), 16) + ur_align_up((size_t)(nbins + 1) * 4, 16) +
+         (size_t)nbins * 8;
+}
+
+template <int N>
+static ur_status launch_cols_n(int mode, const ColArgs& a, cudaStream_t s) {
+  constexpr int T = N / 8, TX = 512 / T;
+  const size_t smem = cols_smem<N>(a.nbins);
+  const int grid = (int)((a.ncols + TX - 1) / TX);
+  if (grid <= 0) return UR_OK;
+#define UR_P2_LAUNCH(MD)                                                                                   \
+  do {                                                                                                     \
+    UR_CUDA_CHECK(cudaFuncSetAttribute(k_p2_cols<N, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_p2_cols<N, MD><<<grid, 512, smem, s>>>(a);                                                           \
+  } while (0)
+  switch (mode) {
+    case P2_Y_FWD: UR_P2_LAUNCH(P2_Y_FWD); break;
+    case P2_Y_INV: UR_P2_LAUNCH(P2_Y_INV); break;
+    case P2_Z_BIN: UR_P2_LAUNCH(P2_Z_BIN); break;
+    default: UR_P2_LAUNCH(P2_Z_ADJ); break;
+  }
+#undef UR_P2_LAUNCH
+  UR_LAUNCH_CHECK("k_p2_cols");
+  return UR_OK;
+}
+
+ur_status ur_fast_cols(int n, int mode, const ColArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 64: return launch_cols_n<64>(mode, a, s);
+    case 128: return launch_cols_n<128>(mode, a, s);
+    case 256: return launch_cols_n<256>(mode, a, s);
+    case 512: return launch_cols_n<512>(mode, a, s);
+    case 1024: return launch_cols_n<1024>(mode, a, s);
+  }
+  ur_set_error("ur_fast_cols: unsupported size %d", n);
+  return UR_ERR_UNSUPPORTED;
+}
+
+template <int N>
+static ur_status launch_rows_n(const RowArgs& a, int gen, int ed_f16, cudaStream_t s) {
+  constexpr int M = N / 2, T = M / 8, RB = 512 / T;
+  const int grid = (int)((a.nrows + RB - 1) / RB);
+  if (grid <= 0) return UR_OK;
+  if (gen) k_p2_rows<N, 1, float><<<grid, 512, 0, s>>>(a);
+  else if (ed_f16) k_p2_rows<N, 0, __half><<<grid, 512, 0, s>>>(a);
+  else k_p2_rows<N, 0, float><<<grid, 512, 0, s>>>(a);
+  UR_LAUNCH_CHECK("k_p2_rows");
+  return UR_OK;
+}
+
+ur_status ur_fast_rows(int n, const RowArgs& a, int gen, int ed_f16, cudaStream_t s) {
+  switch (n) {
+    case 64: return launch_rows_n<64>(a, gen, ed_f16, s);
+    case 128: return launch_rows_n<128>(a, gen, ed_f16, s);
+    case 256: return launch_rows_n<256>(a, gen, ed_f16, s);
+    case 512: return launch_rows_n<512>(a, gen, ed_f16, s);
+    case 1024: return launch_rows_n<1024>(a, gen, ed_f16, s);
+  }
+  ur_set_error("ur_fast_rows: unsupported size %d", n);
+  return UR_ERR_UNSUPPORTED;
+}
+
+template <int N>
+static ur_status launch_grad_n(GradArgs a, int nplanes, cudaStream_t s) {
+  constexpr int M = N / 2, T = M / 8, PITCH = P2<M>::PITCH + 1;
+  const int U = a.ucell;
+  const int rows_per_group = (N + U - 1) / U;
+  int rb = 512 / T;
+  if (rb > rows_per_group) rb = rows_per_group;
+  a.rb = rb;
+  const size_t smem = ur_align_up((size_t)rb * PITCH * sizeof(float2), 16) + (size_t)U * sizeof(float);
+  UR_REQUIRE(smem <= 200 * 1024, "adjoint rows: cell edge %d too large", U);
+  if (smem > 48 * 1024) UR_CUDA_CHECK(cudaFuncSetAttribute(k_p2_rows_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((rows_per_group + rb - 1) / rb), (unsigned)U, (unsigned)nplanes);
+  if (nplanes <= 0) return UR_OK;
+  k_p2_rows_grad<N><<<grid, rb * T, smem, s>>>(a);
+  UR_LAUNCH_CHECK("k_p2_rows_grad");
+  return UR_OK;
+}
+
+ur_status ur_fast_rows_grad(int n, const GradArgs& a, int nplanes, cudaStream_t s) {
+  switch (n) {
+    case 64: return launch_grad_n<64>(a, nplanes, s);
+    case 128: return launch_grad_n<128>(a, nplanes, s);
+    case 256: return launch_grad_n<256>(a, nplanes, s);
+    case 512: return launch_grad_n<512>(a, nplanes, s);
+    case 1024: return launch_grad_n<1024>(a, nplanes, s);
+  }
+  ur_set_error("ur_fast_rows_grad: unsupported size %d", n);
+  return UR_ERR_UNSUPPORTED;
+}

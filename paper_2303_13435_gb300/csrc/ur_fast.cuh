@@ -1,0 +1,37 @@
+// Argument blocks and host entry points of the power-of-two kernels.
+#pragma once
+
+#include "ur_forward.cuh"
+#include "ur_density.cuh"
+
+struct RowArgs {
+  const void* ed;          // density rows (GEN = 0), plane-major, nrows x N
+  float2* X;               // output half-spectrum rows, nrows x (N/2+1)
+  long long nrows;
+  int z0;                  // absolute plane index of row 0 / N (GEN = 1)
+  const float* cell;       // GEN = 1: unit cell U^3
+  int ucell, ox, oy, oz;
+  ShapeArgs sh;
+  const float* weights;    // GEN = 1 with UR_SHAPE_WEIGHTS: full-box weights
+  const float2* tw;        // table exp(-2 pi i t / N), t < N
+};
+
+struct GradArgs {
+  const float2* Y;         // inverse-transformed rows (along z and y), planes [ybase_z, ...)
+  int ybase_z;
+  int z0;                  // first absolute plane of this launch
+  int rb;                  // rows per block (set by the launcher)
+  const float2* tw;
+  const float* cell;
+  int ucell, ox, oy, oz;
+  ShapeArgs sh;
+  const float* weights;
+  float inv_n3;
+  float* dl_dmask;
+  float* dl_dcell;
+};
+
+bool ur_fast_supported(int n);
+ur_status ur_fast_rows(int n, const RowArgs& a, int gen, int ed_f16, cudaStream_t s);
+ur_status ur_fast_cols(int n, int mode, const ColArgs& a, cudaStream_t s);
+ur_status ur_fast_rows_grad(int n, const GradArgs& a, int nplanes, cudaStream_t s);

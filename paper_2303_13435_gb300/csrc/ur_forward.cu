@@ -19,7 +19,7 @@
 #include <stdio.h>
 #include <string.h>
 
-#include "ur_forward.cuh"
+#include "ur_fast.cuh"
 
 #define BIN_CHUNK 8  // consecutive |kz| per thread in the binning walk
 
@@ -42,11 +42,15 @@ __device__ __forceinline__ float2 load_pair<__half>(const __half* p) {
   return __half22float2(h);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_rows_r2c(const T* __restrict__ ed, float2* __restrict__ X, long long nrows,
-                                                  int N, int RB, const StageInfo* __restrict__ sched, int nst,
-                                                  const float2* __restrict__ tw) {
+// GEN = 1: the row's density is generated here (Sec. 2.3 tile + mask) instead of read.
+template <int GEN, typename T>
+__global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, const StageInfo* __restrict__ sched,
+                                                     int nst) {
   extern __shared__ float2 smem[];
+  const T* __restrict__ ed = reinterpret_cast<const T*>(ra.ed);
+  float2* __restrict__ X = ra.X;
+  const long long nrows = ra.nrows;
+  const float2* __restrict__ tw = ra.tw;
   const int M = N >> 1, H = M + 1;
   const long long r0 = (long long)blockIdx.x * RB;
   const FastDiv dm((uint32_t)M), dh((uint32_t)H);
@@ -54,7 +58,26 @@ __global__ void __launch_bounds__(256, 2) k_rows_r2c(const T* __restrict__ ed, f
     const int t = (int)dm.div((uint32_t)f);
     const int m = f - t * M;
     const long long r = r0 + t;
-    smem[f] = (r < nrows) ? load_pair<T>(ed + r * N + 2 * m) : make_float2(0.f, 0.f);
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nrows) {
+      if (GEN) {
+        const int p = (int)(r / N), y = (int)(r - (long long)p * N), z = ra.z0 + p, x = 2 * m, U = ra.ucell;
+        const float* crow = ra.cell + ((long long)((z + ra.oz) % U) * U + (y + ra.oy) % U) * U;
+        float m0, m1;
+        if (ra.weights) {
+          const float2 mw = __ldg(reinterpret_cast<const float2*>(ra.weights + ((long long)z * N + y) * N + x));
+          m0 = mw.x;
+          m1 = mw.y;
+        } else {
+          m0 = mask_at(ra.sh, x, y, z);
+          m1 = mask_at(ra.sh, x + 1, y, z);
+        }
+        v = make_float2(__fmul_rn(__ldg(crow + (x + ra.ox) % U), m0), __fmul_rn(__ldg(crow + (x + 1 + ra.ox) % U), m1));
+      } else {
+        v = load_pair<T>(ed + r * N + 2 * m);
+      }
+    }
+    smem[f] = v;
   }
   __syncthreads();
   fft_lines<false, UR_EMAX>(smem, M, RB, sched, nst, tw);
@@ -368,7 +391,20 @@ __global__ void k_geo_to_double(const unsigned long long* __restrict__ c, double
   if (j < nb) out[j] = (double)c[j];
 }
 
+__global__ void k_binlut(const int32_t* __restrict__ thr, int nb, int smax, int16_t* __restrict__ lut) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > smax) return;
+  const int b = bin_search(thr, nb, s);
+  lut[s] = (int16_t)((b >= 0 && b < nb) ? b : -1);
+}
+
 ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s) {
+  {
+    const int smax = 3 * (p->n / 2) * (p->n / 2);
+    UR_CUDA_CHECK(cudaMalloc(&p->binlut, sizeof(int16_t) * ((size_t)smax + 1)));
+    k_binlut<<<(smax + 256) / 256, 256, 0, s>>>(p->thr, p->nbins, smax, p->binlut);
+    UR_LAUNCH_CHECK("k_binlut");
+  }
   const int nb = p->nbins;
   unsigned long long* cnt = nullptr;
   UR_CUDA_CHECK(cudaMalloc(&cnt, sizeof(unsigned long long) * nb));
@@ -453,8 +489,9 @@ ur_status ur_configure_kernels(ur_plan* p) {
     ur_set_error("ur_plan_create: %d bins need %zu bytes of shared memory per block (max 227 KB)", p->nbins, p->colbin_smem);
     return UR_ERR_UNSUPPORTED;
   }
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZBIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->colbin_smem));
@@ -471,6 +508,15 @@ ur_status ur_configure_kernels(ur_plan* p) {
   p->ws_sigma = (size_t)p->nbins * sizeof(float);
   p->slab_planes = 0;
   p->ws_slab = 0;
+  // power-of-two kernels; plane chunks of about 24 MB stay in L2 between the
+  // row pass and the y-column pass (and between the adjoint's y and row passes)
+  p->fast = ur_fast_supported(n) ? 1 : 0;
+  const size_t plane_bytes = (size_t)n * p->H * sizeof(float2);
+  int ch = (int)((24u << 20) / plane_bytes);
+  if (ch < 1) ch = 1;
+  if (ch > n) ch = n;
+  p->chunk_planes = ch;
+  p->ws_chunk = p->fast ? (size_t)ch * plane_bytes : 0;
   return UR_OK;
 }
 
@@ -497,42 +543,71 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.nst = p->sched_n.nst;
   a.tw = p->tw;
   a.thr = p->thr;
+  a.lut = p->binlut;
   a.nbins = p->nbins;
   a.fin_mul = 1.f;
   return a;
 }
 
-// Pass 1 over rows [0, nrows) of a slab of planes `ed` into X (same plane order).
-ur_status ur_plane_pass(const ur_plan* p, const void* ed, long long nplanes, float2* X, cudaStream_t s) {
-  const long long nrows = nplanes * p->n;
-  const int grid_rows = (int)((nrows + p->row_rb - 1) / p->row_rb);
-  const StageInfo* sm = p->d_sched + UR_MAX_STAGES;
-  ur_timing_begin("rows_r2c", s);
-  if (p->ed_dtype == UR_F32)
-    k_rows_r2c<float><<<grid_rows, p->row_threads, p->row_smem, s>>>((const float*)ed, X, nrows, p->n, p->row_rb, sm,
-                                                                     p->sched_m.nst, p->tw);
-  else
-    k_rows_r2c<__half><<<grid_rows, p->row_threads, p->row_smem, s>>>((const __half*)ed, X, nrows, p->n, p->row_rb, sm,
-                                                                      p->sched_m.nst, p->tw);
-  UR_LAUNCH_CHECK("k_rows_r2c");
-  ur_timing_end(s);
-  ColArgs a = ur_col_args(p);
-  a.src = X;
-  a.dst = X;
-  a.ncols = nplanes * p->H;
-  a.A = (long long)p->n * p->H;
-  a.S = p->H;
-  a.Ad = a.A;
-  a.Sd = a.S;
-  a.nload = p->n;
-  a.zoff = 0;
-  a.nbins = 0;
-  const long long ntiles = (a.ncols + a.TX - 1) / a.TX;
-  ur_timing_begin("cols_y", s);
-  k_cols<COL_Y, false><<<(int)ntiles, p->col_threads, p->col_smem, s>>>(a);
-  UR_LAUNCH_CHECK("k_cols<COL_Y>");
-  ur_timing_end(s);
+// Pass 1 (rows along x, then columns along y) of nplanes planes into X (same
+// plane order).  ra carries either the density rows (GEN = 0) or the density
+// description (GEN = 1, rows generated in the kernel); ra.z0 is the absolute
+// plane of X's first plane.  On the power-of-two path the planes go in chunks
+// whose intermediate stays in L2 between the two kernels.
+static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long nplanes, float2* X, cudaStream_t s) {
+  const int n = p->n, H = p->H;
+  const long long step = p->fast ? p->chunk_planes : nplanes;
+  for (long long p0 = 0; p0 < nplanes; p0 += step) {
+    const long long np = (p0 + step <= nplanes) ? step : nplanes - p0;
+    RowArgs r = ra;
+    r.X = X + p0 * n * H;
+    r.nrows = np * n;
+    r.z0 = ra.z0 + (int)p0;
+    if (!gen) r.ed = (const char*)ra.ed + p0 * (long long)n * n * (p->ed_dtype == UR_F16 ? 2 : 4);
+    ur_timing_begin("rows_r2c", s);
+    if (p->fast) {
+      UR_TRY(ur_fast_rows(n, r, gen, p->ed_dtype == UR_F16, s));
+    } else {
+      const int grid_rows = (int)((r.nrows + p->row_rb - 1) / p->row_rb);
+      const StageInfo* sm = p->d_sched + UR_MAX_STAGES;
+      if (gen) k_rows_r2c<1, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
+      else if (p->ed_dtype == UR_F32)
+        k_rows_r2c<0, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
+      else k_rows_r2c<0, __half><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
+      UR_LAUNCH_CHECK("k_rows_r2c");
+    }
+    ur_timing_end(s);
+    ColArgs a = ur_col_args(p);
+    a.src = r.X;
+    a.dst = r.X;
+    a.ncols = np * H;
+    a.A = (long long)n * H;
+    a.S = H;
+    a.Ad = a.A;
+    a.Sd = a.S;
+    a.nload = n;
+    a.zoff = 0;
+    a.nbins = 0;
+    ur_timing_begin("cols_y", s);
+    if (p->fast) {
+      UR_TRY(ur_fast_cols(n, 0 /* y forward */, a, s));
+    } else {
+      const long long ntiles = (a.ncols + a.TX - 1) / a.TX;
+      k_cols<COL_Y, false><<<(int)ntiles, p->col_threads, p->col_smem, s>>>(a);
+      UR_LAUNCH_CHECK("k_cols<COL_Y>");
+    }
+    ur_timing_end(s);
+  }
   return UR_OK;
+}
+
+ur_status ur_plane_pass(const ur_plan* p, const void* ed, long long nplanes, float2* X, cudaStream_t s) {
+  RowArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.ed = ed;
+  ra.tw = p->tw;
+  ra.z0 = p->z0;
+  return plane_pass(p, ra, 0, nplanes, X, s);
 }
 
 // Pass 2 (+ binning) from the intermediate X holding planes [z0, z0+nz).
@@ -557,8 +632,12 @@ ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2
     a.nbins = 0;
   }
   ur_timing_begin("cols_z_bin", s);
-  k_cols<COL_ZBIN, false><<<p->zbin_grid, p->col_threads, p->colbin_smem, s>>>(a);
-  UR_LAUNCH_CHECK("k_cols<COL_ZBIN>");
+  if (p->fast) {
+    UR_TRY(ur_fast_cols(p->n, 2 /* z + bins */, a, s));
+  } else {
+    k_cols<COL_ZBIN, false><<<p->zbin_grid, p->col_threads, p->colbin_smem, s>>>(a);
+    UR_LAUNCH_CHECK("k_cols<COL_ZBIN>");
+  }
   ur_timing_end(s);
   if (bins) {
     ur_timing_begin("finalize", s);
@@ -580,6 +659,39 @@ extern "C" ur_status ur_fft_intensity(const ur_plan* p, const void* ed, int32_t 
   UR_TRY(ur_fault_point("fft_intensity"));
   float2* X = (float2*)ws;
   UR_TRY(ur_plane_pass(p, ed, p->nz, X, s));
+  UR_TRY(ur_column_pass(p, X, bins, (float2*)F_out, s));
+  return UR_OK;
+}
+
+extern "C" ur_status ur_fft_intensity_tiled(const ur_plan* p, const float* cell, int32_t ucell, const int32_t* origin,
+                                            const ur_shape* shape, const float* weights, double* bins, void* F_out,
+                                            void* ws, size_t ws_bytes, void* stream) {
+  UR_REQUIRE(p && cell && shape && ws, "ur_fft_intensity_tiled: null argument");
+  UR_REQUIRE(ucell >= 1, "ur_fft_intensity_tiled: empty cell");
+  UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_fft_intensity_tiled: bad shape kind");
+  UR_REQUIRE(shape->kind != UR_SHAPE_WEIGHTS || weights, "ur_fft_intensity_tiled: weights required for UR_SHAPE_WEIGHTS");
+  UR_REQUIRE(!weights || ((uintptr_t)weights % 8) == 0, "ur_fft_intensity_tiled: weights must be 8-byte aligned");
+  UR_REQUIRE(ws_bytes >= ur_workspace_size(p, UR_WS_FORWARD), "ur_fft_intensity_tiled: workspace %zu < %zu bytes",
+             ws_bytes, ur_workspace_size(p, UR_WS_FORWARD));
+  UR_REQUIRE(((uintptr_t)ws % 256) == 0, "ur_fft_intensity_tiled: misaligned ws");
+  UR_TRY(ur_fault_point("fft_intensity"));
+  cudaStream_t s = (cudaStream_t)stream;
+  RowArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.tw = p->tw;
+  ra.z0 = p->z0;
+  ra.cell = cell;
+  ra.ucell = ucell;
+  if (origin) {
+    UR_REQUIRE(origin[0] >= 0 && origin[1] >= 0 && origin[2] >= 0, "ur_fft_intensity_tiled: origin must be >= 0");
+    ra.ox = origin[0];
+    ra.oy = origin[1];
+    ra.oz = origin[2];
+  }
+  ra.sh = ur_shape_args(shape);
+  ra.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;
+  float2* X = (float2*)ws;
+  UR_TRY(plane_pass(p, ra, 1, p->nz, X, s));
   UR_TRY(ur_column_pass(p, X, bins, (float2*)F_out, s));
   return UR_OK;
 }

@@ -27,6 +27,7 @@ struct ColArgs {
   const float2* tw;
   // binning
   const int32_t* thr;
+  const int16_t* lut;  // k^2 -> bin (-1 outside)
   int nbins;
   float iscale;      // I' = |F~|^2 * iscale (I' = N^3 I)
   double* gsum;      // [nbins] sum of w I'

@@ -211,6 +211,7 @@ static void plan_free(ur_plan* p) {
   if (p->thr) cudaFree(p->thr);
   if (p->geo) cudaFree(p->geo);
   if (p->d_sched) cudaFree(p->d_sched);
+  if (p->binlut) cudaFree(p->binlut);
   free(p->thr_host);
   free(p);
 }
@@ -335,7 +336,8 @@ extern "C" size_t ur_workspace_size(const ur_plan* p, int32_t what) {
   if (!p) return 0;
   size_t b = 0;
   if (what & (UR_WS_FORWARD | UR_WS_BACKWARD)) b += ur_align_up(p->ws_inter, 256);
-  if (what & UR_WS_BACKWARD) b += ur_align_up(p->ws_inv, 256) + ur_align_up(p->ws_sigma, 256);
+  if (what & UR_WS_BACKWARD)
+    b += ur_align_up(p->ws_inv, 256) + ur_align_up(p->ws_sigma, 256) + ur_align_up(p->ws_chunk, 256);
   if (what & UR_WS_HOST_SLABS) b += 2 * ur_align_up(p->ws_slab, 256);
   return b;
 }

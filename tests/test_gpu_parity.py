@@ -255,3 +255,121 @@ def test_backward_matches_oracle_gradient(mode):
     em = normwise(dmask.cpu().numpy(), gm)
     print(mode, "dL/du", eu, "dL/dm", em)
     assert eu <= GRAD_RTOL and em <= GRAD_RTOL
+
+
+# ---------------------------------------------------------------------------
+# Fused density + transform (density generated inside the plane pass)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["sc64", "mof128_cube_origin", "mof256_sphere", "mof96_generic", "mof128_weights"])
+def test_tiled_forward_matches_oracle(case):
+    weights = None
+    if case == "sc64":
+        w = inputs.sc64_workload()
+    elif case == "mof128_cube_origin":
+        w = mof(128, 70, kind=inputs.SHAPE_CUBE, rot_seed=4, origin=(5, 1, 9))
+    elif case == "mof256_sphere":
+        w = mof(256, 120)
+    elif case == "mof96_generic":
+        w = mof(96, 50, kind=inputs.SHAPE_OCTAHEDRON, rot_seed=8)
+    else:
+        w = mof(128, 60)
+        weights = np.random.default_rng(6).random((128, 128, 128)).astype(np.float32)
+        weights[:20] = 0
+        weights[100:] = 0
+        w.shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
+    rho = oracle_density(w, weights=weights)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    gb = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, origin=w.origin,
+                                 weights=dev(weights) if weights is not None else None).cpu().numpy()
+    rep = compare_bins(gb, oracle_forward(rho, w.dx, w.edges), rho.astype(np.float64), case)
+    # the stored-ED path gives the same bins
+    gb2 = api.fft_intensity(plan, dev(rho[z0:z0 + nz])).cpu().numpy()
+    assert np.allclose(gb2[4], gb[4], rtol=1e-6, equal_nan=True)
+    print(case, rep)
+
+
+def test_n1024_sampled_F_parseval_and_counts():
+    """Largest power-of-two size: sampled F against the direct Eq. 1 sum, Parseval over
+    bins that cover the whole grid, and exact bin counts."""
+    w = mof(1024, 180)
+    n = w.n
+    edges = inputs.log_edges(2 * math.pi / (n * w.dx) * 0.99, math.sqrt(3) * math.pi / w.dx * 1.001, 300)
+    edges = np.concatenate([[0.0], edges])
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(n, w.dx, edges, z0=z0, nz=nz)
+    F = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+    gb = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, F_out=F).cpu().numpy()
+    rng = np.random.default_rng(0)
+    ks = np.stack([rng.integers(0, n // 2 + 1, 24), rng.integers(-n // 2, n // 2, 24), rng.integers(-n // 2, n // 2, 24)], 1)
+    ks[0] = (0, 0, 0)
+    ks[1] = (3, -2, 1)
+    want = scatter.dft_at(rho[z0:z0 + nz], ks, z_begin=z0)
+    got = F[ks[:, 2] % n, ks[:, 1] % n, ks[:, 0]].cpu().numpy()
+    got = got[:, 0] + 1j * got[:, 1]
+    scale = abs(want[0])
+    assert np.max(np.abs(got - want)) <= 1e-5 * scale
+    r64 = rho[z0:z0 + nz].astype(np.float64)
+    parseval = float((r64 ** 2).sum()) / float(n) ** 3  # Parseval under Eq. 1: sum_k |F_k|^2 = sum rho^2 / N^3
+    tot = float(np.nansum(gb[1]))
+    assert math.isclose(tot, parseval, rel_tol=1e-5)
+    # the edges cover every |Q| of the grid, so the counts add up to N^3 exactly
+    assert int(gb[0].sum()) == n ** 3
+
+
+@pytest.mark.parametrize("case", ["mof128_weights_origin", "mof256_chunks", "sc64_tiled"])
+def test_backward_fast_path(case):
+    weights = None
+    if case == "mof128_weights_origin":
+        w = mof(128, 60, ucell=32, a_nm=1.3, origin=(3, 0, 7))
+        weights = np.random.default_rng(7).random((128, 128, 128)).astype(np.float32)
+        weights[:30] = 0
+        weights[98:] = 0
+        w.shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
+    elif case == "mof256_chunks":
+        w = mof(256, 110, kind=inputs.SHAPE_CUBE, rot_seed=3)
+    else:
+        w = inputs.sc64_workload()
+    rho = oracle_density(w, weights=weights)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    wd = dev(weights) if weights is not None else None
+    bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, origin=w.origin, weights=wd, ws=ws)
+    gb = bins.cpu().numpy()
+    g = np.where(gb[0] > 0, 1.0 / np.maximum(np.nan_to_num(gb[4]), 1e-300), 0.0) * 1e-3
+    dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws, origin=w.origin, weights=wd)
+    mask = density.mask_values(w.n, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot, weights)
+    ob_count = oracle_forward(rho, w.dx, w.edges)["count"]
+    gu, gm = oracle_grads(rho.astype(np.float64), w.cell.astype(np.float64), mask, w.dx, w.edges, g, ob_count,
+                          w.origin)
+    eu = normwise(dcell.cpu().numpy(), gu)
+    em = normwise(dmask.cpu().numpy(), gm)
+    print(case, "dL/du", eu, "dL/dm", em)
+    assert eu <= GRAD_RTOL and em <= GRAD_RTOL
+
+
+def test_mof512_full_size_forward_and_adjoint():
+    """The 512^3 workload of the benchmark, in its launch configuration (fused tiled
+    forward, recomputing adjoint), against the FP64 oracle."""
+    w = inputs.mof_workload(n=512, diameter_nm=10.0, nbins=512)
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    assert nz == 247
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, ws=ws)
+    gb = bins.cpu().numpy()
+    r64 = rho.astype(np.float64)
+    ob = oracle_forward(r64, w.dx, w.edges)
+    rep = compare_bins(gb, ob, r64, "mof512")
+    print("mof512 forward", rep)
+    g = np.where(gb[0] > 0, 1.0 / np.maximum(np.nan_to_num(gb[4]), 1e-300), 0.0) * 1e-3
+    dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws)
+    mask = density.mask_values(w.n, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot)
+    gu, gm = oracle_grads(r64, w.cell.astype(np.float64), mask, w.dx, w.edges, g, ob["count"])
+    eu = normwise(dcell.cpu().numpy(), gu)
+    em = normwise(dmask.cpu().numpy(), gm)
+    print("mof512 adjoint", eu, em)
+    assert eu <= GRAD_RTOL and em <= GRAD_RTOL
