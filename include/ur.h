@@ -178,6 +178,30 @@ ur_status ur_fft_intensity_tiled(const ur_plan* plan, const float* cell, int32_t
                                  const ur_shape* shape, const float* weights, double* bins, void* F_out, void* ws,
                                  size_t ws_bytes, void* stream);
 
+/* ur_fft_intensity_noalloc -- the paper has no counterpart; this entry point
+ * serves callers that must not allocate device memory while they run (a
+ * real-time or embedded loop with a memory budget fixed at start-up, a
+ * plugin whose host program owns all device allocations, or code that cannot
+ * call the CUDA allocator).  It computes what ur_fft_intensity computes with
+ * F_out = NULL, but keeps the plane-transform intermediate in a scratch
+ * array built into the library instead of a caller workspace, and it calls no
+ * allocator itself.  The plan is still created beforehand (that allocates
+ * the plan's tables once).
+ *   - Limit: the intermediate, nz * N * (N/2+1) * 8 bytes, must fit
+ *     UR_NOALLOC_SCRATCH_BYTES (64 MiB); larger plans get UR_ERR_INVALID
+ *     and a message naming both sizes.
+ *   - Every GPU that loads the library reserves those 64 MiB until the
+ *     process exits.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (two streams at once) race and
+ *     give wrong results; serialise them.
+ *   ed: device planes [z0, z0+nz), ed_dtype; bins: device double[6][B]. */
+#define UR_NOALLOC_SCRATCH_BYTES (64u << 20)
+ur_status ur_fft_intensity_noalloc(const ur_plan* plan, const void* ed, double* bins, void* stream);
+
 /* Sec. 2.5 binning of a stored half-spectrum intensity I[kz][ky][kx]
  * (device float32, N*N*(N/2+1), Eq. 1 normalised); kx in (0, N/2) weighs 2
  * (the mirrored half), kx = 0 and N/2 weigh 1.  ws: ur_workspace_size(plan, UR_WS_FORWARD). */

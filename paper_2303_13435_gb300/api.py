@@ -50,6 +50,7 @@ SIGNATURES = {
     "ur_fft_intensity": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
     "ur_fft_intensity_tiled": (_i32, [_vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp, _vp,
                                       _sz, _vp]),
+    "ur_fft_intensity_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "ur_bin_q": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _vp, _vp]),
     "ur_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
@@ -234,6 +235,18 @@ def fft_intensity_tiled(plan: Plan, cell: torch.Tensor, shape, origin=(0, 0, 0),
     _check("ur_fft_intensity_tiled", lib().ur_fft_intensity_tiled(plan.handle, _ptr(cell), cell.shape[0], org,
                                                                   C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
                                                                   _ptr(ws), ws.numel(), _stream(stream)))
+    return bins
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def fft_intensity_noalloc(plan: Plan, ed: torch.Tensor, bins: torch.Tensor, stream=None) -> torch.Tensor:
+    """ur_fft_intensity without a workspace, for callers that must not allocate while
+    running: the intermediate sits in the library's built-in 64 MiB scratch array.
+    `bins` must be preallocated by the caller; calls that overlap on the GPU race."""
+    _check("ur_fft_intensity_noalloc", lib().ur_fft_intensity_noalloc(plan.handle, _ptr(ed), _ptr(bins),
+                                                                      _stream(stream)))
     return bins
 
 
