@@ -119,6 +119,10 @@ enum { UR_WS_FORWARD = 1, UR_WS_BACKWARD = 2, UR_WS_HOST_SLABS = 4 };
  * adds two staging slabs for ED read from pinned host memory. */
 size_t ur_workspace_size(const ur_plan* plan, int32_t what);
 
+/* Planes per host->device slab of the out-of-core path (default: about
+ * 256 MiB of ED per slab).  Changes ur_workspace_size(plan, UR_WS_HOST_SLABS). */
+ur_status ur_plan_set_slab_planes(ur_plan* plan, int32_t planes);
+
 /* ---------------------------------------------------------------------------
  * ur_build_density (Sec. 2.3).
  * ------------------------------------------------------------------------- */

@@ -44,6 +44,7 @@ SIGNATURES = {
     "ur_bin_thresholds": (_i32, [_i32, C.c_double, _dp, _i32, C.POINTER(C.c_int64)]),
     "ur_fault_reset": (None, []),
     "ur_workspace_size": (_sz, [_vp, _i32]),
+    "ur_plan_set_slab_planes": (_i32, [_vp, _i32]),
     "ur_build_density": (_i32, [_i32, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _i32, _i32, _i32,
                                 _vp, _vp, _vp]),
     "ur_zoom_density": (_i32, [_i32, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -158,6 +159,9 @@ class Plan:
 
     def workspace_size(self, what: int = UR_WS_FORWARD) -> int:
         return int(lib().ur_workspace_size(self._h, what))
+
+    def set_slab_planes(self, planes: int):
+        _check("ur_plan_set_slab_planes", lib().ur_plan_set_slab_planes(self._h, int(planes)))
 
     def workspace(self, what: int = UR_WS_FORWARD, device="cuda") -> torch.Tensor:
         return torch.empty(self.workspace_size(what), dtype=torch.uint8, device=device)

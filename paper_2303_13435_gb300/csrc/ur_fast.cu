@@ -28,7 +28,8 @@
 template <int L>
 struct P2 {
   static constexpr int LOG = L == 8 ? 3 : L == 16 ? 4 : L == 32 ? 5 : L == 64 ? 6 : L == 128 ? 7 : L == 256 ? 8
-                                                                                           : L == 512 ? 9 : L == 1024 ? 10 : 11;
+                                                                                           : L == 512 ? 9 : L == 1024 ? 10
+                                                                                           : L == 2048 ? 11 : 12;
   static constexpr int T = L / 8;
   static constexpr int NFULL = LOG / 3;
   static constexpr int REM = LOG % 3;
@@ -37,6 +38,15 @@ struct P2 {
 };
 
 __device__ __forceinline__ int p2pad(int i) { return i + (i >> 4); }
+
+// smallest r >= 0 with r*r >= v, for 0 <= v < 2^24 (float sqrt is within one of it)
+__device__ __forceinline__ int isqrt_ceil(int v) {
+  if (v <= 0) return 0;
+  int r = (int)sqrtf((float)v);
+  while (r * r < v) ++r;
+  while (r > 0 && (r - 1) * (r - 1) >= v) --r;
+  return r;
+}
 
 constexpr int ipow8(int s) { return s == 0 ? 1 : 8 * ipow8(s - 1); }
 
@@ -131,12 +141,15 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
     const int U = a.ucell;
     const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
     const float* wrow = a.weights ? a.weights + ((long long)z * N + y) * N : nullptr;
+    // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
+    const int cstep = (2 * T) % U;
+    int c0 = (2 * j + a.ox) % U;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int x = 2 * (j + q * T);
       float e0 = 0.f, e1 = 0.f;
+      const int c1 = c0 + 1 == U ? 0 : c0 + 1;
       if (valid) {
-        const int c0 = (x + a.ox) % U, c1 = (x + 1 + a.ox) % U;
         float m0, m1;
         if (wrow) {
           const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
@@ -150,6 +163,8 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
         e1 = __fmul_rn(__ldg(crow + c1), m1);
       }
       v[q] = make_float2(e0, e1);
+      c0 += cstep;
+      if (c0 >= U) c0 -= U;
     }
   } else {
     const TED* row = reinterpret_cast<const TED*>(a.ed) + r * N;
@@ -198,10 +213,18 @@ __device__ __forceinline__ void p2_bins8(int c2, int j, const int16_t* __restric
   }
 }
 
+// threads per column block: 512, or 1024 for N >= 2048 so that a block still
+// spans at least two columns (16-byte row segments) of the half spectrum
+template <int N>
+struct ColCfg {
+  static constexpr int THREADS = N >= 2048 ? 1024 : 512;
+  static constexpr int TX = THREADS / (N / 8);
+};
+
 template <int N, int MODE>
-__global__ void __launch_bounds__(512) k_p2_cols(ColArgs a) {
+__global__ void __launch_bounds__(ColCfg<N>::THREADS) k_p2_cols(ColArgs a) {
   // column pitch = 2 (mod 16) float2: the TX columns a warp touches fall on different banks
-  constexpr int T = N / 8, TX = 512 / T, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
+  constexpr int T = N / 8, TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_blo, s_bhi;
   float2* buf = reinterpret_cast<float2*>(smraw);
@@ -268,7 +291,13 @@ __global__ void __launch_bounds__(512) k_p2_cols(ColArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
       __syncthreads();
-      constexpr int NCH = (H + BIN_CHUNK_F - 1) / BIN_CHUNK_F;
+      // task = (column, chunk of CH consecutive |kz| = m); one task per thread at most.
+      // Inside a chunk the bin changes only where c2 + m^2 crosses the next threshold,
+      // found from the threshold itself (integer square root), so the inner loop over a
+      // run of equal bins only loads and accumulates.
+      constexpr int CH = (H + T - 1) / T;
+      constexpr int NCH = (H + CH - 1) / CH;
+      const int nb = a.nbins;
       for (int task = threadIdx.x; task < TX * NCH; task += blockDim.x) {
         const int tc = task % TX, ch = task / TX;
         const int gcol = col0 + tc;
@@ -277,34 +306,39 @@ __global__ void __launch_bounds__(512) k_p2_cols(ColArgs a) {
         const int cc2 = kx2 * kx2 + ky2 * ky2;
         const float w = (kx2 == 0 || kx2 == M) ? 1.f : 2.f;
         const float2* ln = buf + tc * PITCH;
-        const int m0 = ch * BIN_CHUNK_F, m1 = min(m0 + BIN_CHUNK_F, M + 1);
-        int run = __ldg(a.lut + cc2 + m0 * m0);
-        float sI = 0.f, sI2 = 0.f;
-        for (int m = m0; m < m1; ++m) {
-          const int cur = __ldg(a.lut + cc2 + m * m);
-          if (cur != run) {
-            if (run >= 0 && run < a.nbins) {
-              atomicAdd(hs + run, w * sI);
-              atomicAdd(hs2 + run, w * sI2);
+        const int m1 = min(ch * CH + CH, M + 1);
+        int m = ch * CH;
+        while (m < m1) {
+          const int s = cc2 + m * m;
+          int b = -1, mend;
+          if (s < thr[0]) {
+            mend = isqrt_ceil(thr[0] - cc2);
+          } else if (s >= thr[nb]) {
+            mend = m1;
+          } else {
+            b = __ldg(a.lut + s);
+            mend = isqrt_ceil(thr[b + 1] - cc2);
+          }
+          if (mend > m1) mend = m1;
+          if (mend <= m) mend = m + 1;
+          if (b >= 0) {
+            float sI = 0.f, sI2 = 0.f;
+            for (int mm = m; mm < mend; ++mm) {
+              const float2 f1 = ln[p2pad(mm)];
+              const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
+              sI += i1;
+              sI2 += i1 * i1;
+              if (mm != 0 && mm != M) {
+                const float2 f2 = ln[p2pad(N - mm)];
+                const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
+                sI += i2;
+                sI2 += i2 * i2;
+              }
             }
-            run = cur;
-            sI = 0.f;
-            sI2 = 0.f;
+            atomicAdd(hs + b, w * sI);
+            atomicAdd(hs2 + b, w * sI2);
           }
-          const float2 f1 = ln[p2pad(m)];
-          const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
-          sI += i1;
-          sI2 += i1 * i1;
-          if (m != 0 && m != M) {
-            const float2 f2 = ln[p2pad(N - m)];
-            const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
-            sI += i2;
-            sI2 += i2 * i2;
-          }
-        }
-        if (run >= 0 && run < a.nbins) {
-          atomicAdd(hs + run, w * sI);
-          atomicAdd(hs2 + run, w * sI2);
+          m = mend;
         }
       }
       __syncthreads();
@@ -376,11 +410,16 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
   const float* wrow = a.weights ? a.weights + ((long long)z * N + (valid ? y : 0)) * N : nullptr;
   if (valid) {
     float* drow = a.dl_dmask ? a.dl_dmask + ((long long)z * N + y) * N : nullptr;
+    // cell columns of x = 2 (j + q T): one modulo, then steps of 2T mod U; when U divides
+    // 2T they are the same for every q and the dL/du sums stay in two registers
+    const int cstep = (2 * T) % U;
+    int c0 = (2 * j + a.ox) % U;
+    float r0 = 0.f, r1 = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int x = 2 * (j + q * T);
       const float g0 = v[q].x * a.inv_n3, g1 = v[q].y * a.inv_n3;
-      const int c0 = (x + a.ox) % U, c1 = (x + 1 + a.ox) % U;
+      const int c1 = c0 + 1 == U ? 0 : c0 + 1;
       if (drow) *reinterpret_cast<float2*>(drow + x) = make_float2(g0 * __ldg(crow + c0), g1 * __ldg(crow + c1));
       float m0, m1;
       if (wrow) {
@@ -391,8 +430,19 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
         m0 = rm.at(x);
         m1 = rm.at(x + 1);
       }
-      if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
-      if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
+      if (cstep == 0) {
+        r0 += g0 * m0;
+        r1 += g1 * m1;
+      } else {
+        if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
+        if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
+      }
+      c0 += cstep;
+      if (c0 >= U) c0 -= U;
+    }
+    if (cstep == 0) {
+      if (r0 != 0.f) atomicAdd(acc + c0, r0);
+      if (r1 != 0.f) atomicAdd(acc + (c0 + 1 == U ? 0 : c0 + 1), r1);
     }
   }
   __syncthreads();
@@ -403,25 +453,27 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
 // ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
-bool ur_fast_supported(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+bool ur_fast_supported(int n) {
+  return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096;
+}
 
 template <int N>
 static size_t cols_smem(int nbins) {
-  constexpr int T = N / 8, TX = 512 / T, PITCH = P2<N>::PITCH + 2;
+  constexpr int TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2;
   return ur_align_up((size_t)TX * PITCH * sizeof(float2), 16) + ur_align_up((size_t)(nbins + 1) * 4, 16) +
          (size_t)nbins * 8;
 }
 
 template <int N>
 static ur_status launch_cols_n(int mode, const ColArgs& a, cudaStream_t s) {
-  constexpr int T = N / 8, TX = 512 / T;
+  constexpr int TX = ColCfg<N>::TX;
   const size_t smem = cols_smem<N>(a.nbins);
   const int grid = (int)((a.ncols + TX - 1) / TX);
   if (grid <= 0) return UR_OK;
 #define UR_P2_LAUNCH(MD)                                                                                   \
   do {                                                                                                     \
     UR_CUDA_CHECK(cudaFuncSetAttribute(k_p2_cols<N, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k_p2_cols<N, MD><<<grid, 512, smem, s>>>(a);                                                           \
+    k_p2_cols<N, MD><<<grid, ColCfg<N>::THREADS, smem, s>>>(a);                                                           \
   } while (0)
   switch (mode) {
     case P2_Y_FWD: UR_P2_LAUNCH(P2_Y_FWD); break;
@@ -441,6 +493,8 @@ ur_status ur_fast_cols(int n, int mode, const ColArgs& a, cudaStream_t s) {
     case 256: return launch_cols_n<256>(mode, a, s);
     case 512: return launch_cols_n<512>(mode, a, s);
     case 1024: return launch_cols_n<1024>(mode, a, s);
+    case 2048: return launch_cols_n<2048>(mode, a, s);
+    case 4096: return launch_cols_n<4096>(mode, a, s);
   }
   ur_set_error("ur_fast_cols: unsupported size %d", n);
   return UR_ERR_UNSUPPORTED;
@@ -465,6 +519,8 @@ ur_status ur_fast_rows(int n, const RowArgs& a, int gen, int ed_f16, cudaStream_
     case 256: return launch_rows_n<256>(a, gen, ed_f16, s);
     case 512: return launch_rows_n<512>(a, gen, ed_f16, s);
     case 1024: return launch_rows_n<1024>(a, gen, ed_f16, s);
+    case 2048: return launch_rows_n<2048>(a, gen, ed_f16, s);
+    case 4096: return launch_rows_n<4096>(a, gen, ed_f16, s);
   }
   ur_set_error("ur_fast_rows: unsupported size %d", n);
   return UR_ERR_UNSUPPORTED;
@@ -495,6 +551,8 @@ ur_status ur_fast_rows_grad(int n, const GradArgs& a, int nplanes, cudaStream_t 
     case 256: return launch_grad_n<256>(a, nplanes, s);
     case 512: return launch_grad_n<512>(a, nplanes, s);
     case 1024: return launch_grad_n<1024>(a, nplanes, s);
+    case 2048: return launch_grad_n<2048>(a, nplanes, s);
+    case 4096: return launch_grad_n<4096>(a, nplanes, s);
   }
   ur_set_error("ur_fast_rows_grad: unsupported size %d", n);
   return UR_ERR_UNSUPPORTED;

@@ -506,8 +506,15 @@ ur_status ur_configure_kernels(ur_plan* p) {
   p->ws_inter = (size_t)p->nz * n * p->H * sizeof(float2);
   p->ws_inv = (size_t)n * n * p->H * sizeof(float2);
   p->ws_sigma = (size_t)p->nbins * sizeof(float);
-  p->slab_planes = 0;
-  p->ws_slab = 0;
+  // host-resident ED: slabs of about 256 MiB, two of them in the workspace
+  {
+    const size_t ed_plane = (size_t)n * n * (p->ed_dtype == UR_F16 ? 2 : 4);
+    long long sp = (long long)((256ull << 20) / ed_plane);
+    if (sp < 1) sp = 1;
+    if (sp > p->nz) sp = p->nz;
+    p->slab_planes = (int)sp;
+    p->ws_slab = (size_t)sp * ed_plane;
+  }
   // power-of-two kernels; plane chunks of about 24 MB stay in L2 between the
   // row pass and the y-column pass (and between the adjoint's y and row passes)
   p->fast = ur_fast_supported(n) ? 1 : 0;
