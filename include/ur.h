@@ -259,14 +259,43 @@ void ur_set_timing(int32_t enable);
 int32_t ur_last_timings(float* ms_out, int32_t max_entries, const char** names_out);
 
 /* ---------------------------------------------------------------------------
- * Batched particles (uneven grid sizes).  All plans must share the bin edges'
- * count B.  eds[i], bins[i] follow ur_fft_intensity for plans[i] (device ED).
- * ws: ur_batch_workspace_size bytes.  The forward launches one kernel per
- * pass for the whole batch; ur_batch_backward mirrors ur_backward.
+ * Batched particles of uneven grid sizes (Sec. 3: polydispersity as many
+ * particle simulations).  A batch is built once from its items; afterwards
+ * ur_batch_forward runs the tiled forward (density generated in the plane
+ * pass, transform, |F|^2, bins) of every item and ur_batch_backward the adjoint
+ * of every item, each as a fixed sequence of five kernel launches whose
+ * blocks cover all items (no host work in between, so the pair can be
+ * captured in one CUDA graph).  Items keep their buffers for the life of the
+ * batch.  The batch uses the runtime-radix kernels for every grid edge.
  * ------------------------------------------------------------------------- */
-size_t ur_batch_workspace_size(int32_t count, const ur_plan* const* plans, int32_t what);
-ur_status ur_batch_forward(int32_t count, const ur_plan* const* plans, const void* const* eds,
-                           double* const* bins, void* ws, size_t ws_bytes, void* stream);
+typedef struct ur_batch ur_batch;
+typedef struct {
+  const ur_plan* plan;     /* grid, plane slab and bins of this particle */
+  const float* cell;       /* device float32 U^3 */
+  int32_t ucell;
+  int32_t origin[3];
+  ur_shape shape;
+  const float* weights;    /* device N^3, UR_SHAPE_WEIGHTS only */
+  double* bins;            /* device double[UR_BIN_FIELDS][B]: forward output */
+  void* ws;                /* device workspace, 256-byte aligned */
+  size_t ws_bytes;         /* >= ur_workspace_size(plan, UR_WS_FORWARD | UR_WS_BACKWARD) (FORWARD only without adjoint) */
+  const double* dl_dmean;  /* device double[B]: adjoint input, or NULL (no adjoint) */
+  float* dl_dcell;         /* device float32 U^3: adjoint output, or NULL */
+  float* dl_dmask;         /* device float32 N^3: adjoint output, or NULL */
+} ur_batch_item;
+
+ur_status ur_batch_create(int32_t count, const ur_batch_item* items, ur_batch** out);
+ur_status ur_batch_destroy(ur_batch* batch);
+ur_status ur_batch_forward(const ur_batch* batch, void* stream);
+ur_status ur_batch_backward(const ur_batch* batch, void* stream);
+
+/* Tile shape of the runtime-radix kernels of a plan (the autotuner's knob):
+ * rows per block of the row passes and columns per block of the column
+ * passes; 0 keeps the current value.  rows * N/2 and cols * N must not exceed
+ * 4096 (elements held by a 256-thread block).  Takes effect for later calls
+ * and for batches created afterwards. */
+ur_status ur_plan_set_tiles(ur_plan* plan, int32_t rows_per_block, int32_t cols_per_block);
+ur_status ur_plan_get_tiles(const ur_plan* plan, int32_t* rows_per_block, int32_t* cols_per_block);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,13 @@ class ShapeDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("center", C.c_float * 3), ("size", C.c_float), ("rot", C.c_float * 9)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("cell", C.c_void_p), ("ucell", C.c_int32), ("origin", C.c_int32 * 3),
+                ("shape", ShapeDesc), ("weights", C.c_void_p), ("bins", C.c_void_p), ("ws", C.c_void_p),
+                ("ws_bytes", C.c_size_t), ("dl_dmean", C.c_void_p), ("dl_dcell", C.c_void_p),
+                ("dl_dmask", C.c_void_p)]
+
+
 SIGNATURES = {
     "ur_last_error": (C.c_char_p, []),
     "ur_version": (C.c_char_p, []),
@@ -58,8 +65,12 @@ SIGNATURES = {
                            _vp, _sz, _vp]),
     "ur_set_timing": (None, [_i32]),
     "ur_last_timings": (_i32, [C.POINTER(C.c_float), _i32, C.POINTER(C.c_char_p)]),
-    "ur_batch_workspace_size": (_sz, [_i32, C.POINTER(_vp), _i32]),
-    "ur_batch_forward": (_i32, [_i32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp, _sz, _vp]),
+    "ur_batch_create": (_i32, [_i32, _vp, C.POINTER(_vp)]),
+    "ur_batch_destroy": (_i32, [_vp]),
+    "ur_batch_forward": (_i32, [_vp, _vp]),
+    "ur_batch_backward": (_i32, [_vp, _vp]),
+    "ur_plan_set_tiles": (_i32, [_vp, _i32, _i32]),
+    "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
 # test hooks (not part of the header's API)
 EXTRA = {
@@ -159,6 +170,14 @@ class Plan:
 
     def workspace_size(self, what: int = UR_WS_FORWARD) -> int:
         return int(lib().ur_workspace_size(self._h, what))
+
+    def set_tiles(self, rows_per_block: int = 0, cols_per_block: int = 0):
+        _check("ur_plan_set_tiles", lib().ur_plan_set_tiles(self._h, int(rows_per_block), int(cols_per_block)))
+
+    def tiles(self) -> tuple[int, int]:
+        r, c = C.c_int32(), C.c_int32()
+        _check("ur_plan_get_tiles", lib().ur_plan_get_tiles(self._h, C.byref(r), C.byref(c)))
+        return r.value, c.value
 
     def set_slab_planes(self, planes: int):
         _check("ur_plan_set_slab_planes", lib().ur_plan_set_slab_planes(self._h, int(planes)))
@@ -301,6 +320,66 @@ def bin_thresholds(n: int, dx: float, edges) -> np.ndarray:
     _check("ur_bin_thresholds", lib().ur_bin_thresholds(n, dx, e.ctypes.data_as(_dp), len(e) - 1,
                                                         out.ctypes.data_as(C.POINTER(C.c_int64))))
     return out
+
+
+class Batch:
+    """ur_batch over particles of uneven grids: one forward and one adjoint launch
+    sequence for all of them.  Each particle: a Plan, the cell (device float32
+    U^3), a Shape, and optional adjoint buffers; the batch allocates (via torch)
+    each particle's bins, workspace, dL/dmean input and dL/d cell output."""
+
+    def __init__(self, plans, cells, shapes, origins=None, with_backward=True, with_mask_grad=False):
+        self.plans = list(plans)
+        n = len(self.plans)
+        self.cells = list(cells) if isinstance(cells, (list, tuple)) else [cells] * n
+        self.shapes = list(shapes)
+        origins = origins or [(0, 0, 0)] * n
+        what = UR_WS_FORWARD | (UR_WS_BACKWARD if with_backward else 0)
+        self.bins = [new_bins(p) for p in self.plans]
+        self.ws = [p.workspace(what) for p in self.plans]
+        self.dl_dmean = [torch.zeros(p.nbins, dtype=torch.float64, device="cuda") if with_backward else None
+                         for p in self.plans]
+        self.dl_dcell = [torch.zeros_like(c) if with_backward else None for c in self.cells]
+        self.dl_dmask = [torch.zeros((p.n, p.n, p.n), dtype=torch.float32, device="cuda")
+                         if (with_backward and with_mask_grad) else None for p in self.plans]
+        items = (BatchItem * n)()
+        for i in range(n):
+            it = items[i]
+            it.plan = self.plans[i].handle.value
+            it.cell = self.cells[i].data_ptr()
+            it.ucell = self.cells[i].shape[0]
+            for a in range(3):
+                it.origin[a] = int(origins[i][a])
+            it.shape = shape_desc(self.shapes[i])
+            it.weights = None
+            it.bins = self.bins[i].data_ptr()
+            it.ws = self.ws[i].data_ptr()
+            it.ws_bytes = self.ws[i].numel()
+            it.dl_dmean = self.dl_dmean[i].data_ptr() if with_backward else None
+            it.dl_dcell = self.dl_dcell[i].data_ptr() if with_backward else None
+            it.dl_dmask = self.dl_dmask[i].data_ptr() if self.dl_dmask[i] is not None else None
+        h = C.c_void_p()
+        _check("ur_batch_create", lib().ur_batch_create(n, C.cast(items, C.c_void_p), C.byref(h)))
+        self._h = h
+
+    def forward(self, stream=None):
+        _check("ur_batch_forward", lib().ur_batch_forward(self._h, _stream(stream)))
+        return self.bins
+
+    def backward(self, stream=None):
+        _check("ur_batch_backward", lib().ur_batch_backward(self._h, _stream(stream)))
+        return self.dl_dcell
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ur_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_timing(enable: bool):

@@ -36,21 +36,27 @@ __global__ void k_sigma(const double* __restrict__ g, const double* __restrict__
 // Each row: Y[z][y][0..M] (Hermitian half along x) -> Z[k] = E[k] + i O[k],
 //   E[k] = X[k] + conj X[M-k],  O[k] = (X[k] - conj X[M-k]) conj(W_N^k),
 // then z = IFFT_{M}(Z) gives (g(2m), g(2m+1)) = (Re z[m], Im z[m]).
-__global__ void __launch_bounds__(256, 2) k_rows_grad(const float2* __restrict__ Y, int N, int RB,
-                                                   const StageInfo* __restrict__ sched, int nst,
-                                                   const float2* __restrict__ tw, const float* __restrict__ cell, int U,
-                                                   int ox, int oy, int oz, ShapeArgs sh, const float* __restrict__ weights,
-                                                   float inv_n3, float* __restrict__ dl_dmask, float* __restrict__ dl_dcell) {
+__device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int by) {
+  const float2* __restrict__ Y = g.Y;
+  const int N = g.N, RB = g.RB, nst = g.nst, U = g.U, ox = g.ox, oy = g.oy, oz = g.oz;
+  const StageInfo* __restrict__ sched = g.sched;
+  const float2* __restrict__ tw = g.tw;
+  const float* __restrict__ cell = g.cell;
+  const ShapeArgs& sh = g.sh;
+  const float* __restrict__ weights = g.weights;
+  const float inv_n3 = g.inv_n3;
+  float* __restrict__ dl_dmask = g.dl_dmask;
+  float* __restrict__ dl_dcell = g.dl_dcell;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int M = N >> 1, H = M + 1;
   float2* buf = reinterpret_cast<float2*>(smraw);
   float* acc = reinterpret_cast<float*>(smraw + ur_align_up_dev((size_t)RB * H * sizeof(float2), 16));
-  const int cz = blockIdx.y / U, cy = blockIdx.y - (blockIdx.y / U) * U;
+  const int cz = by / U, cy = by - (by / U) * U;
   const int zf = ((cz - oz) % U + U) % U, yf = ((cy - oy) % U + U) % U;
   const int nzr = zf < N ? (N - 1 - zf) / U + 1 : 0;
   const int nyr = yf < N ? (N - 1 - yf) / U + 1 : 0;
   const int nrows = nzr * nyr;
-  const int r0 = blockIdx.x * RB;
+  const int r0 = bx * RB;
   if (r0 >= nrows) return;  // uniform over the block
   for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
   const float* crow = cell + ((long long)cz * U + cy) * U;
@@ -132,6 +138,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_grad(const float2* __restrict__
   for (int i = threadIdx.x; i < U; i += blockDim.x)
     if (acc[i] != 0.f) atomicAdd(dl_dcell + ((long long)cz * U + cy) * U + i, acc[i]);
 }
+
+__global__ void __launch_bounds__(256, 2) k_rows_grad(GenGradArgs g) { rows_grad_body(g, blockIdx.x, blockIdx.y); }
 
 extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const double* fwd_bins, const void* F,
                                  const float* cell, int32_t ucell, const int32_t* origin, const ur_shape* shape,
@@ -266,9 +274,70 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
   dim3 ggrid((unsigned)((rows_per_group + RB - 1) / RB), (unsigned)(ucell * ucell));
   UR_CUDA_CHECK(cudaMemsetAsync(dl_dcell, 0, sizeof(float) * (size_t)ucell * ucell * ucell, s));
   ur_timing_begin("adj_rows_grad", s);
-  k_rows_grad<<<ggrid, 256, smem, s>>>(Y, n, RB, p->d_sched + UR_MAX_STAGES, p->sched_m.nst, p->tw, cell, ucell,
-                                               ox, oy, oz, sh, weights, (float)(1.0 / n3), dl_dmask, dl_dcell);
+  GenGradArgs ga;
+  memset(&ga, 0, sizeof ga);
+  ga.Y = Y;
+  ga.N = n;
+  ga.RB = RB;
+  ga.nst = p->sched_m.nst;
+  ga.sched = p->d_sched + UR_MAX_STAGES;
+  ga.tw = p->tw;
+  ga.cell = cell;
+  ga.U = ucell;
+  ga.ox = ox;
+  ga.oy = oy;
+  ga.oz = oz;
+  ga.sh = sh;
+  ga.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;
+  ga.inv_n3 = (float)(1.0 / n3);
+  ga.dl_dmask = dl_dmask;
+  ga.dl_dcell = dl_dcell;
+  k_rows_grad<<<ggrid, 256, smem, s>>>(ga);
   UR_LAUNCH_CHECK("k_rows_grad");
   ur_timing_end(s);
+  return UR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched adjoint launches
+// ---------------------------------------------------------------------------
+__global__ void k_batch_sigma(const BatchSigmaItem* __restrict__ items) {
+  const BatchSigmaItem& it = items[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= it.nb) return;
+  const double n = it.bins[UR_BIN_COUNT * it.nb + j];
+  it.sigma[j] = (float)(n > 0 ? 2.0 * it.g[j] / n / it.n3 : 0.0);
+}
+
+__global__ void __launch_bounds__(256, 2) k_batch_grad(const BatchGradItem* __restrict__ items,
+                                                       const long long* __restrict__ start, int count) {
+  int lo = 0, hi = count - 1;
+  const long long b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchGradItem& it = items[lo];
+  const long long local = b - __ldg(start + lo);
+  const int gx = it.gx;
+  rows_grad_body(it.g, (int)(local % gx), (int)(local / gx));
+}
+
+ur_status ur_batch_launch_sigma(const BatchSigmaItem* items, int count, int maxnb, cudaStream_t s) {
+  if (count <= 0) return UR_OK;
+  k_batch_sigma<<<dim3((unsigned)((maxnb + 255) / 256), (unsigned)count), 256, 0, s>>>(items);
+  UR_LAUNCH_CHECK("k_batch_sigma");
+  return UR_OK;
+}
+
+ur_status ur_batch_launch_grad(const BatchGradItem* items, const long long* start, int count, long long nblocks,
+                               size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return UR_OK;
+  UR_REQUIRE(nblocks < (1ll << 31), "batched adjoint rows: too many blocks");
+  if (smem > 48 * 1024)
+    UR_CUDA_CHECK(cudaFuncSetAttribute(k_batch_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_batch_grad<<<(unsigned)nblocks, 256, smem, s>>>(items, start, count);
+  UR_LAUNCH_CHECK("k_batch_grad");
   return UR_OK;
 }

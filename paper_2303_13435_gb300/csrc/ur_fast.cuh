@@ -31,6 +31,13 @@ struct GradArgs {
   float* dl_dcell;
 };
 
+// one item of a batched generic row pass
+struct BatchRowsItem {
+  RowArgs ra;
+  int N, RB, nst, gen;
+  const StageInfo* sched;
+};
+
 bool ur_fast_supported(int n);
 ur_status ur_fast_rows(int n, const RowArgs& a, int gen, int ed_f16, cudaStream_t s);
 ur_status ur_fast_cols(int n, int mode, const ColArgs& a, cudaStream_t s);

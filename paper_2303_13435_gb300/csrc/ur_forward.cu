@@ -43,16 +43,17 @@ __device__ __forceinline__ float2 load_pair<__half>(const __half* p) {
 }
 
 // GEN = 1: the row's density is generated here (Sec. 2.3 tile + mask) instead of read.
+// Body of one block (block index blk); shared by the single-plan and batched launches.
 template <int GEN, typename T>
-__global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, const StageInfo* __restrict__ sched,
-                                                     int nst) {
+__device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, const StageInfo* __restrict__ sched,
+                                              int nst, long long blk) {
   extern __shared__ float2 smem[];
   const T* __restrict__ ed = reinterpret_cast<const T*>(ra.ed);
   float2* __restrict__ X = ra.X;
   const long long nrows = ra.nrows;
   const float2* __restrict__ tw = ra.tw;
   const int M = N >> 1, H = M + 1;
-  const long long r0 = (long long)blockIdx.x * RB;
+  const long long r0 = blk * RB;
   const FastDiv dm((uint32_t)M), dh((uint32_t)H);
   for (int f = threadIdx.x; f < RB * M; f += blockDim.x) {
     const int t = (int)dm.div((uint32_t)f);
@@ -95,6 +96,12 @@ __global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, 
     const float2 w = __ldg(tw + k);
     X[r * H + k] = cadd(e, cmul(w, o));
   }
+}
+
+template <int GEN, typename T>
+__global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, const StageInfo* __restrict__ sched,
+                                                     int nst) {
+  rows_r2c_body<GEN, T>(ra, N, RB, sched, nst, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,7 +231,7 @@ struct SigmaScale {
 // One block per tile of TX columns.  (A persistent loop over tiles around the
 // shared-memory FFT made the compiler spill ~1.3 KB per thread.)
 template <int MODE, bool INV>
-__global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
+__device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_blo, s_bhi;
   float2* buf = reinterpret_cast<float2*>(smraw);
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
   int32_t* thr = reinterpret_cast<int32_t*>(smraw + buf_bytes);
   double* hs = nullptr;
   double* hs2 = nullptr;
-  const long long c0 = (long long)blockIdx.x * a.TX;
+  const long long c0 = blk * a.TX;
   if (MODE != COL_Y && a.nbins > 0) {
     for (int j = threadIdx.x; j <= a.nbins; j += blockDim.x) thr[j] = __ldg(a.thr + j);
     if (MODE == COL_ZBIN) {
@@ -300,12 +307,17 @@ __global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
   }
 }
 
+template <int MODE, bool INV>
+__global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
+  cols_body<MODE, INV>(a, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Finalize: bins[UR_BIN_FIELDS][B] from the accumulated sums (in I' units:
 // I' = N^3 I) and the plan's per-bin count and sum |Q|.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(double* __restrict__ bins, const double* __restrict__ geo, int nb, double inv_n3) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void finalize_bin(double* __restrict__ bins, const double* __restrict__ geo, int nb,
+                                             double inv_n3, int j) {
   if (j >= nb) return;
   const double n = geo[j];
   const double s = bins[UR_BIN_SUM_I * nb + j] * inv_n3;
@@ -324,6 +336,10 @@ __global__ void k_finalize(double* __restrict__ bins, const double* __restrict__
   }
   bins[UR_BIN_MEAN * nb + j] = mean;
   bins[UR_BIN_SEM * nb + j] = sem;
+}
+
+__global__ void k_finalize(double* __restrict__ bins, const double* __restrict__ geo, int nb, double inv_n3) {
+  finalize_bin(bins, geo, nb, inv_n3, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,13 +505,16 @@ ur_status ur_configure_kernels(ur_plan* p) {
     ur_set_error("ur_plan_create: %d bins need %zu bytes of shared memory per block (max 227 KB)", p->nbins, p->colbin_smem);
     return UR_ERR_UNSUPPORTED;
   }
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->row_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZBIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->colbin_smem));
-  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZADJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->col_smem));
+  // the runtime-radix kernels accept any tile shape up to the per-block limit
+  // (ur_plan_set_tiles may change it), so they get the largest dynamic size once
+  const int kMaxDyn = 200 * 1024;
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZBIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZADJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   const long long ntiles = ((long long)n * p->H + p->col_tx - 1) / p->col_tx;
   p->zbin_grid = (int)ntiles;
   // device copy of the radix schedules
@@ -718,5 +737,91 @@ extern "C" ur_status ur_bin_q(const ur_plan* p, const float* I, double* bins, vo
   UR_LAUNCH_CHECK("k_bin_half");
   k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
   UR_LAUNCH_CHECK("k_finalize");
+  return UR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches (many plans of different grid edges in one grid).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_item(const long long* __restrict__ start, int count, long long b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256, 2) k_batch_rows(const BatchRowsItem* __restrict__ items,
+                                                       const long long* __restrict__ start, int count) {
+  const int i = batch_item(start, count, blockIdx.x);
+  const BatchRowsItem& it = items[i];
+  if (it.gen) rows_r2c_body<1, float>(it.ra, it.N, it.RB, it.sched, it.nst, blockIdx.x - __ldg(start + i));
+  else rows_r2c_body<0, float>(it.ra, it.N, it.RB, it.sched, it.nst, blockIdx.x - __ldg(start + i));
+}
+
+template <int MODE, bool INV>
+__global__ void __launch_bounds__(256, 2) k_batch_cols(const ColArgs* __restrict__ items,
+                                                       const long long* __restrict__ start, int count) {
+  const int i = batch_item(start, count, blockIdx.x);
+  cols_body<MODE, INV>(items[i], blockIdx.x - __ldg(start + i));
+}
+
+__global__ void k_batch_finalize(const BatchFinItem* __restrict__ items) {
+  const BatchFinItem& it = items[blockIdx.y];
+  finalize_bin(it.bins, it.geo, it.nb, it.inv_n3, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_batch_zero(const BatchZeroItem* __restrict__ items) {
+  const BatchZeroItem& it = items[blockIdx.y];
+  const size_t n4 = it.bytes / 4;
+  uint32_t* p = reinterpret_cast<uint32_t*>(it.ptr);
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (size_t)gridDim.x * blockDim.x) p[k] = 0u;
+}
+
+static void batch_grid_check(long long nblocks) { (void)nblocks; }
+
+ur_status ur_batch_launch_rows(const BatchRowsItem* items, const long long* start, int count, long long nblocks,
+                               size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return UR_OK;
+  UR_REQUIRE(nblocks < (1ll << 31), "batched rows: too many blocks");
+  batch_grid_check(nblocks);
+  if (smem > 48 * 1024)
+    UR_CUDA_CHECK(cudaFuncSetAttribute(k_batch_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_batch_rows<<<(unsigned)nblocks, 256, smem, s>>>(items, start, count);
+  UR_LAUNCH_CHECK("k_batch_rows");
+  return UR_OK;
+}
+
+ur_status ur_batch_launch_cols(int mode, bool inv, const ColArgs* items, const long long* start, int count,
+                               long long nblocks, size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return UR_OK;
+  UR_REQUIRE(nblocks < (1ll << 31), "batched columns: too many blocks");
+#define UR_BATCH_COLS(MD, IV)                                                                                  \
+  do {                                                                                                         \
+    UR_CUDA_CHECK(cudaFuncSetAttribute(k_batch_cols<MD, IV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_batch_cols<MD, IV><<<(unsigned)nblocks, 256, smem, s>>>(items, start, count);                            \
+  } while (0)
+  if (mode == COL_Y && !inv) UR_BATCH_COLS(COL_Y, false);
+  else if (mode == COL_Y) UR_BATCH_COLS(COL_Y, true);
+  else if (mode == COL_ZBIN) UR_BATCH_COLS(COL_ZBIN, false);
+  else UR_BATCH_COLS(COL_ZADJ, false);
+#undef UR_BATCH_COLS
+  UR_LAUNCH_CHECK("k_batch_cols");
+  return UR_OK;
+}
+
+ur_status ur_batch_launch_finalize(const BatchFinItem* items, int count, int maxnb, cudaStream_t s) {
+  if (count <= 0) return UR_OK;
+  k_batch_finalize<<<dim3((unsigned)((maxnb + 255) / 256), (unsigned)count), 256, 0, s>>>(items);
+  UR_LAUNCH_CHECK("k_batch_finalize");
+  return UR_OK;
+}
+
+ur_status ur_batch_launch_zero(const BatchZeroItem* items, int count, cudaStream_t s) {
+  if (count <= 0) return UR_OK;
+  k_batch_zero<<<dim3(64u, (unsigned)count), 256, 0, s>>>(items);
+  UR_LAUNCH_CHECK("k_batch_zero");
   return UR_OK;
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "ur_common.cuh"
+#include "ur_density.cuh"
 
 #define UR_EMAX 16  // elements per thread in the shared-memory FFT engine
 
@@ -39,6 +40,59 @@ struct ColArgs {
   float fin_mul;       // multiplier applied to every loaded element
   int skip_fwd;        // 1: the loaded column is already the spectrum along z
 };
+
+// generic adjoint row pass (one block: a batch of rows wrapping onto one cell row)
+struct GenGradArgs {
+  const float2* Y;
+  int N, RB, nst;
+  const StageInfo* sched;
+  const float2* tw;
+  const float* cell;
+  int U, ox, oy, oz;
+  ShapeArgs sh;
+  const float* weights;
+  float inv_n3;
+  float* dl_dmask;
+  float* dl_dcell;
+};
+
+// ---------------------------------------------------------------------------
+// Batched launches: one grid covers the blocks of every item; block b belongs
+// to item i with start[i] <= b < start[i+1] (device tables built once).
+// ---------------------------------------------------------------------------
+struct RowArgs;
+struct BatchRowsItem;
+struct BatchFinItem {
+  double* bins;
+  const double* geo;
+  int nb;
+  double inv_n3;
+};
+struct BatchSigmaItem {
+  const double* g;
+  const double* bins;
+  int nb;
+  double n3;
+  float* sigma;
+};
+struct BatchZeroItem {
+  void* ptr;
+  size_t bytes;
+};
+struct BatchGradItem {
+  GenGradArgs g;
+  int gx;  // blocks along the row batches of one cell row
+};
+
+ur_status ur_batch_launch_rows(const BatchRowsItem* items, const long long* start, int count, long long nblocks,
+                               size_t smem, cudaStream_t s);
+ur_status ur_batch_launch_cols(int mode, bool inv, const ColArgs* items, const long long* start, int count,
+                               long long nblocks, size_t smem, cudaStream_t s);
+ur_status ur_batch_launch_finalize(const BatchFinItem* items, int count, int maxnb, cudaStream_t s);
+ur_status ur_batch_launch_sigma(const BatchSigmaItem* items, int count, int maxnb, cudaStream_t s);
+ur_status ur_batch_launch_zero(const BatchZeroItem* items, int count, cudaStream_t s);
+ur_status ur_batch_launch_grad(const BatchGradItem* items, const long long* start, int count, long long nblocks,
+                               size_t smem, cudaStream_t s);
 
 ColArgs ur_col_args(const ur_plan* p);
 ur_status ur_plane_pass(const ur_plan* p, const void* ed, long long nplanes, float2* X, cudaStream_t s);
