@@ -75,6 +75,7 @@ SIGNATURES = {
 # test hooks (not part of the header's API)
 EXTRA = {
     "ur_selftest_fastdiv": (C.c_int64, []),
+    "ur_selftest_dft": (C.c_double, []),
 }
 
 _lib = None

@@ -76,18 +76,20 @@ struct FastDiv {
 };
 
 // ---------------------------------------------------------------------------
-// Complex helpers (float2 = re, im)
+// Complex helpers (float2 = re, im); host-callable so the library can check its
+// butterflies against a direct DFT without a GPU.
+#define UR_HD __host__ __device__
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+UR_HD __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+UR_HD __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+UR_HD __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+UR_HD __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+UR_HD __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // a * (-i) for the forward direction, a * (+i) for the inverse
 template <bool INV>
-__device__ __forceinline__ float2 mul_ni(float2 a) {
+UR_HD __forceinline__ float2 mul_ni(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 // Twiddle load through the read-only path.  The asm is volatile so that the
@@ -100,7 +102,7 @@ __device__ __forceinline__ float2 ld_twiddle(const float2* p) {
 }
 // a * W where W is the forward twiddle (inverse: conj(W))
 template <bool INV>
-__device__ __forceinline__ float2 twmul(float2 a, float2 w) {
+UR_HD __forceinline__ float2 twmul(float2 a, float2 w) {
   return INV ? make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
 }
 
@@ -109,14 +111,14 @@ __device__ __forceinline__ float2 twmul(float2 a, float2 w) {
 // inverse: the conjugate kernel (no scaling).
 // ---------------------------------------------------------------------------
 template <bool INV>
-__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+UR_HD __forceinline__ void dft2(float2& a0, float2& a1) {
   float2 t = a0;
   a0 = cadd(t, a1);
   a1 = csub(t, a1);
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+UR_HD __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
   float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
   float2 t2 = cadd(a1, a3), t3 = mul_ni<INV>(csub(a1, a3));
   a0 = cadd(t0, t2);
@@ -126,7 +128,7 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft8(float2* a) {
+UR_HD __forceinline__ void dft8(float2* a) {
   // even/odd split into two 4-point DFTs, then W8^k combination
   float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
   float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
@@ -158,33 +160,33 @@ template <int R>
 struct OddConst;
 template <>
 struct OddConst<3> {
-  __device__ static constexpr float c(int q) { return -0.5f; }
-  __device__ static constexpr float s(int q) { return q == 1 ? 0.86602540378443865f : -0.86602540378443865f; }
+  __host__ __device__ static constexpr float c(int q) { return -0.5f; }
+  __host__ __device__ static constexpr float s(int q) { return q == 1 ? 0.86602540378443865f : -0.86602540378443865f; }
 };
 template <>
 struct OddConst<5> {
-  __device__ static constexpr float c(int q) {
+  __host__ __device__ static constexpr float c(int q) {
     return (q == 1 || q == 4) ? 0.30901699437494742f : -0.80901699437494742f;
   }
-  __device__ static constexpr float s(int q) {
+  __host__ __device__ static constexpr float s(int q) {
     return q == 1 ? 0.95105651629515357f : q == 2 ? 0.58778525229247313f : q == 3 ? -0.58778525229247313f
                                                                                   : -0.95105651629515357f;
   }
 };
 template <>
 struct OddConst<7> {
-  __device__ static constexpr float c(int q) {
+  __host__ __device__ static constexpr float c(int q) {
     return (q == 1 || q == 6) ? 0.62348980185873353f : (q == 2 || q == 5) ? -0.22252093395631440f
                                                                            : -0.90096886790241913f;
   }
-  __device__ static constexpr float s(int q) {
+  __host__ __device__ static constexpr float s(int q) {
     return q == 1 ? 0.78183148246802981f : q == 2 ? 0.97492791218182361f : q == 3 ? 0.43388373911755812f
            : q == 4 ? -0.43388373911755812f : q == 5 ? -0.97492791218182361f : -0.78183148246802981f;
   }
 };
 
 template <int R, bool INV>
-__device__ __forceinline__ void dft_odd(float2* a) {
+UR_HD __forceinline__ void dft_odd(float2* a) {
   constexpr int h = (R - 1) / 2;
   float2 b[h], d[h];
 #pragma unroll
@@ -224,14 +226,60 @@ __device__ __forceinline__ void dft_odd(float2* a) {
   for (int p = 0; p < R; ++p) a[p] = y[p];
 }
 
+// exp(-2 pi i m / 32) from the first octant of cos(2 pi m / 32) (float64 literals)
+UR_HD constexpr float ur_cos32(int m) {
+  constexpr float c[9] = {1.0f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+                          0.70710678118654752f, 0.55557023301960218f, 0.38268343236508977f, 0.19509032201612825f, 0.0f};
+  m &= 31;
+  return m <= 8 ? c[m] : m <= 16 ? -c[16 - m] : m <= 24 ? -c[m - 16] : c[32 - m];
+}
+UR_HD constexpr float ur_w32_re(int m) { return ur_cos32(m); }
+UR_HD constexpr float ur_w32_im(int m) { return -ur_cos32(m - 8); }  // -sin(2 pi m / 32)
+
+// L = R1 R2 point DFT from R1- and R2-point DFTs (n = R2 n1 + n2, k = k1 + R1 k2):
+//   X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) [W_L^(n2 k1) sum_n1 a[R2 n1 + n2] W_R1^(n1 k1)]
 template <int R, bool INV>
-__device__ __forceinline__ void dft(float2* a) {
+UR_HD __forceinline__ void dft(float2* a);
+
+template <int R1, int R2, bool INV>
+UR_HD __forceinline__ void dft_split(float2* a) {
+  constexpr int L = R1 * R2;
+  float2 y[L];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    float2 t[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) t[n1] = a[R2 * n1 + n2];
+    dft<R1, INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const int m = (n2 * k1 * (32 / L)) & 31;
+      y[n2 * R1 + k1] = (n2 * k1 == 0) ? t[k1] : twmul<INV>(t[k1], make_float2(ur_w32_re(m), ur_w32_im(m)));
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 t[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+    dft<R2, INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = t[k2];
+  }
+}
+
+template <int R, bool INV>
+UR_HD __forceinline__ void dft(float2* a) {
   if constexpr (R == 2) {
     dft2<INV>(a[0], a[1]);
   } else if constexpr (R == 4) {
     dft4<INV>(a[0], a[1], a[2], a[3]);
   } else if constexpr (R == 8) {
     dft8<INV>(a);
+  } else if constexpr (R == 16) {
+    dft_split<4, 4, INV>(a);
+  } else if constexpr (R == 32) {
+    dft_split<4, 8, INV>(a);
   } else {
     dft_odd<R, INV>(a);
   }

@@ -170,6 +170,59 @@ extern "C" int64_t ur_selftest_fastdiv(void) {
   return bad;
 }
 
+// Butterfly check on the host: every compile-time radix of the row and column
+// engines against a direct float64 DFT, forward and inverse, on seeded inputs.
+// Returns the largest error relative to the input's L2 norm.
+template <int R, bool INV>
+static double dft_err(uint64_t& st) {
+  float2 a[R];
+  double re[R], im[R], nrm = 0.0;
+  for (int p = 0; p < R; ++p) {
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    re[p] = (double)(int32_t)(st >> 32) / 2147483648.0;
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    im[p] = (double)(int32_t)(st >> 32) / 2147483648.0;
+    a[p] = make_float2((float)re[p], (float)im[p]);
+    re[p] = a[p].x;
+    im[p] = a[p].y;
+    nrm += re[p] * re[p] + im[p] * im[p];
+  }
+  dft<R, INV>(a);
+  const double sg = INV ? 1.0 : -1.0, tau = 6.283185307179586476925286766559;
+  double err = 0.0;
+  for (int k = 0; k < R; ++k) {
+    double xr = 0.0, xi = 0.0;
+    for (int p = 0; p < R; ++p) {
+      const double ang = sg * tau * (double)((int64_t)p * k % R) / R;
+      xr += re[p] * cos(ang) - im[p] * sin(ang);
+      xi += re[p] * sin(ang) + im[p] * cos(ang);
+    }
+    err = fmax(err, hypot(a[k].x - xr, a[k].y - xi));
+  }
+  return err / sqrt(nrm);
+}
+
+template <int R>
+static double dft_err_both(uint64_t& st) {
+  double e = 0.0;
+  for (int t = 0; t < 8; ++t) e = fmax(e, fmax(dft_err<R, false>(st), dft_err<R, true>(st)));
+  return e;
+}
+
+extern "C" double ur_selftest_dft(void) {
+  uint64_t st = 0x2303134350ULL;
+  double e = 0.0;
+  e = fmax(e, dft_err_both<2>(st));
+  e = fmax(e, dft_err_both<3>(st));
+  e = fmax(e, dft_err_both<4>(st));
+  e = fmax(e, dft_err_both<5>(st));
+  e = fmax(e, dft_err_both<7>(st));
+  e = fmax(e, dft_err_both<8>(st));
+  e = fmax(e, dft_err_both<16>(st));
+  e = fmax(e, dft_err_both<32>(st));
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // Bin thresholds: t_j = min{s >= 0 : dq * sqrt(s) >= e_j} for j < B and
 // t_B = min{s : dq * sqrt(s) > e_B}, in IEEE float64.  fl(dq * fl(sqrt(s))) is

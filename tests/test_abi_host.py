@@ -36,6 +36,14 @@ def test_fastdiv_matches_integer_division():
     assert api.lib().ur_selftest_fastdiv() == 0
 
 
+def test_butterflies_match_direct_dft():
+    # radices 2..32 of the FFT engines, forward and inverse, against a float64
+    # direct DFT; FP32 butterflies with float64 twiddle constants stay within a
+    # few ulp of the input norm
+    err = api.lib().ur_selftest_dft()
+    assert 0.0 <= err < 2e-6, err
+
+
 @pytest.mark.parametrize("n,dx,kind", [(64, 0.0625, "lin"), (512, 0.040625, "log"), (96, 0.05, "log"),
                                        (16, 0.2, "tie")])
 def test_thresholds_reproduce_oracle_bin_of_every_k2(n, dx, kind):
