@@ -54,6 +54,12 @@ struct RowMask {
       rz[a] = __fmul_rn(sh.r[6 + a], dz);
     }
   }
+  // True when the mask is zero at every x of the row.  Sphere only: rounding
+  // to nearest is monotone and fl(dx*dx) >= 0, so fl(fl(fl(dx*dx) + dy2) + dz2)
+  // >= fl(dy2 + dz2) for every x; other shapes report false (no shortcut).
+  __device__ __forceinline__ bool empty() const {
+    return kind == UR_SHAPE_SPHERE && __fadd_rn(dy2, dz2) > s2;
+  }
   __device__ __forceinline__ float at(int x) const {
     if (kind == UR_SHAPE_ALL) return 1.f;
     const float dx = __fsub_rn((float)x, cx);

@@ -73,9 +73,24 @@ __device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const floa
   }
 }
 
+// Barrier between the writers and readers of a line: the whole block, or only
+// the warp when every thread of the line sits in one warp (L/8 <= 32).
+template <bool WS>
+__device__ __forceinline__ void p2_sync(unsigned wmask) {
+  if constexpr (WS) __syncwarp(wmask);
+  else __syncthreads();
+}
+
+// lanes of the warp that hold the line of this thread (L/8 <= 32 threads per line)
+template <int T>
+__device__ __forceinline__ unsigned p2_line_lanes() {
+  if constexpr (T >= 32) return 0xffffffffu;
+  else return ((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1));
+}
+
 // Stage outputs to shared memory at (b - k) R + k + r NS, then reload as j + q L/8.
-template <int L, int R, int NS>
-__device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line) {
+template <int L, int R, int NS, bool WS>
+__device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line, unsigned wmask) {
   constexpr int T = L / 8, NB = 8 / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
@@ -84,30 +99,34 @@ __device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line)
 #pragma unroll
     for (int r = 0; r < R; ++r) line[p2pad((b - k) * R + k + r * NS)] = v[i + NB * r];
   }
-  __syncthreads();
+  p2_sync<WS>(wmask);
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = line[p2pad(j + q * T)];
-  __syncthreads();
+  p2_sync<WS>(wmask);
 }
 
-template <int L, bool INV, int S>
+template <int L, bool INV, bool WS, int S>
 struct P2Run {
-  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws) {
+  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws,
+                                             unsigned wmask) {
     constexpr int NST = P2<L>::NST, NFULL = P2<L>::NFULL, REM = P2<L>::REM;
     if constexpr (S < NST) {
       constexpr int R = (S < NFULL) ? 8 : (1 << REM);
       constexpr int NS = ipow8(S);
       p2_butterflies<L, R, NS, INV>(v, j, tw, tws);
-      if constexpr (S + 1 < NST) p2_exchange<L, R, NS>(v, j, line);
-      P2Run<L, INV, S + 1>::run(v, j, line, tw, tws);
+      if constexpr (S + 1 < NST) p2_exchange<L, R, NS, WS>(v, j, line, wmask);
+      P2Run<L, INV, WS, S + 1>::run(v, j, line, tw, tws, wmask);
     }
   }
 };
 
-// Whole line transform; every thread of the block must call it (it synchronises).
-template <int L, bool INV>
-__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws) {
-  P2Run<L, INV, 0>::run(v, j, line, tw, tws);
+// Whole line transform.  WS = false: every thread of the block must call it
+// (block barriers); WS = true: the L/8 threads of a line share a warp and all
+// of them (the lanes in wmask) must call it.
+template <int L, bool INV, bool WS = false>
+__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws,
+                                       unsigned wmask = 0xffffffffu) {
+  P2Run<L, INV, WS, 0>::run(v, j, line, tw, tws, wmask);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,29 +146,33 @@ __device__ __forceinline__ float2 ld_pair<__half>(const __half* p) {
 template <int N, int GEN, typename TED>
 __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
   constexpr int M = N / 2, H = M + 1, T = M / 8, RB = 512 / T, PITCH = P2<M>::PITCH;
+  // a row of up to 256 complex values is one warp (or part of one): warp barriers only
+  constexpr bool WS = T <= 32;
   __shared__ __align__(16) float2 sm[RB * PITCH];
   const int t = threadIdx.x / T, j = threadIdx.x - (threadIdx.x / T) * T;
   const long long r = (long long)blockIdx.x * RB + t;
   const bool valid = r < a.nrows;
+  const unsigned wmask = p2_line_lanes<T>();
   float2* line = sm + t * PITCH;
   float2 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = make_float2(0.f, 0.f);
   if (GEN) {
     const int p = (int)(r / N), y = (int)(r - (long long)p * N);
     const int z = a.z0 + p;
     RowMask rm;
     rm.init(a.sh, y, z);
     const int U = a.ucell;
-    const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
     const float* wrow = a.weights ? a.weights + ((long long)z * N + y) * N : nullptr;
-    // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
-    const int cstep = (2 * T) % U;
-    int c0 = (2 * j + a.ox) % U;
+    // rows the mask excludes entirely are zero (cell values are finite)
+    if (valid && (wrow || !rm.empty())) {
+      const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
+      // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
+      const int cstep = (2 * T) % U;
+      int c0 = (2 * j + a.ox) % U;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int x = 2 * (j + q * T);
-      float e0 = 0.f, e1 = 0.f;
-      const int c1 = c0 + 1 == U ? 0 : c0 + 1;
-      if (valid) {
+      for (int q = 0; q < 8; ++q) {
+        const int x = 2 * (j + q * T);
         float m0, m1;
         if (wrow) {
           const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
@@ -159,23 +182,32 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
           m0 = rm.at(x);
           m1 = rm.at(x + 1);
         }
-        e0 = __fmul_rn(__ldg(crow + c0), m0);
-        e1 = __fmul_rn(__ldg(crow + c1), m1);
+        const float u0 = __ldg(crow + c0), u1 = __ldg(crow + (c0 + 1 == U ? 0 : c0 + 1));
+        c0 += cstep;
+        if (c0 >= U) c0 -= U;
+        v[q] = make_float2(__fmul_rn(u0, m0), __fmul_rn(u1, m1));
       }
-      v[q] = make_float2(e0, e1);
-      c0 += cstep;
-      if (c0 >= U) c0 -= U;
     }
-  } else {
+  } else if (valid) {
     const TED* row = reinterpret_cast<const TED*>(a.ed) + r * N;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = valid ? ld_pair<TED>(row + 2 * (j + q * T)) : make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) v[q] = ld_pair<TED>(row + 2 * (j + q * T));
   }
-  p2_fft<M, false>(v, j, line, a.tw, 2);
-  // split step: X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2
+  // a row whose values are all zero transforms to zero: skip its butterflies
+  bool zero_row = false;
+  if constexpr (WS) {
+    bool nz = false;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
-  __syncthreads();
+    for (int q = 0; q < 8; ++q) nz |= (v[q].x != 0.f) || (v[q].y != 0.f);
+    zero_row = (__ballot_sync(wmask, nz) & wmask) == 0u;
+  }
+  if (!zero_row) p2_fft<M, false, WS>(v, j, line, a.tw, 2, wmask);
+  // split step: X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2
+  if (!zero_row) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
+  }
+  p2_sync<WS>(wmask);
   if (valid) {
     float2* X = a.X + r * H;
 #pragma unroll
@@ -184,6 +216,10 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
       if (q == 8) {
         if (j != 0) break;
         k = M;
+      }
+      if (zero_row) {
+        X[k] = make_float2(0.f, 0.f);
+        continue;
       }
       const float2 zk = line[p2pad(k == M ? 0 : k)];
       const float2 zc = cconj(line[p2pad(k == 0 ? 0 : M - k)]);
@@ -215,14 +251,17 @@ __device__ __forceinline__ void p2_bins8(int c2, int j, const int16_t* __restric
 
 // threads per column block: 512, or 1024 for N >= 2048 so that a block still
 // spans at least two columns (16-byte row segments) of the half spectrum
-template <int N>
+// MINB: resident blocks per SM the register budget is cut for (the z pass
+// with binning fits in 32 registers: four blocks of 512 threads)
+template <int N, int MODE = P2_Y_FWD>
 struct ColCfg {
   static constexpr int THREADS = N >= 2048 ? 1024 : 512;
   static constexpr int TX = THREADS / (N / 8);
+  static constexpr int MINB = N >= 2048 ? 1 : MODE == P2_Z_BIN ? 4 : 3;
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS) k_p2_cols(ColArgs a) {
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k_p2_cols(ColArgs a) {
   // column pitch = 2 (mod 16) float2: the TX columns a warp touches fall on different banks
   constexpr int T = N / 8, TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -266,11 +305,17 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) k_p2_cols(ColArgs a) {
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
   float2 v[8];
+  if (a.zoff == 0 && a.nload == N) {  // whole column present (y passes, F given)
+    const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);
+    const long long step = (long long)T * a.S;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int li = j + q * T - a.zoff;
-    v[q] = (valid && li >= 0 && li < a.nload) ? __ldg(a.src + sbase + (long long)li * a.S) : make_float2(0.f, 0.f);
-    if (a.fin_mul != 1.f) v[q] = cscale(v[q], a.fin_mul);
+    for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q * step);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int li = j + q * T - a.zoff;
+      v[q] = (valid && li >= 0 && li < a.nload) ? __ldg(a.src + sbase + (long long)li * a.S) : make_float2(0.f, 0.f);
+    }
   }
   float2* line = buf + c * PITCH;
   if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
@@ -374,12 +419,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS) k_p2_cols(ColArgs a) {
 template <int N>
 __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
   constexpr int M = N / 2, H = M + 1, T = M / 8, PITCH = P2<M>::PITCH + 1;
+  constexpr bool WS = T <= 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int RB = a.rb;
   float2* sm = reinterpret_cast<float2*>(smraw);
   float* acc = reinterpret_cast<float*>(smraw + ur_align_up_dev((size_t)RB * PITCH * sizeof(float2), 16));
   const int U = a.ucell;
   const int t = threadIdx.x / T, j = threadIdx.x - (threadIdx.x / T) * T;
+  const unsigned wmask = p2_line_lanes<T>();
   const int cy = blockIdx.y;
   const int z = a.z0 + blockIdx.z;
   const int cz = (z + a.oz) % U;
@@ -390,7 +437,7 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
   float2* line = sm + t * PITCH;
   const float2* Yrow = a.Y + ((long long)(z - a.ybase_z) * N + (valid ? y : 0)) * H;
   for (int k = j; k < H; k += T) line[p2pad(k)] = valid ? __ldg(Yrow + k) : make_float2(0.f, 0.f);
-  __syncthreads();
+  __syncthreads();  // also orders the zeroing of acc before any accumulation
   float2 v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -402,47 +449,68 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
     const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);
     v[q] = make_float2(e.x - o.y, e.y + o.x);
   }
-  __syncthreads();
-  p2_fft<M, true>(v, j, line, a.tw, 2);
+  p2_sync<WS>(wmask);
+  p2_fft<M, true, WS>(v, j, line, a.tw, 2, wmask);
   const float* crow = a.cell + ((long long)cz * U + cy) * U;
   RowMask rm;
   rm.init(a.sh, valid ? y : 0, z);
   const float* wrow = a.weights ? a.weights + ((long long)z * N + (valid ? y : 0)) * N : nullptr;
   if (valid) {
     float* drow = a.dl_dmask ? a.dl_dmask + ((long long)z * N + y) * N : nullptr;
+    // rows the mask excludes entirely add nothing to dL/du
+    const bool mzero = !wrow && rm.empty();
     // cell columns of x = 2 (j + q T): one modulo, then steps of 2T mod U; when U divides
     // 2T they are the same for every q and the dL/du sums stay in two registers
     const int cstep = (2 * T) % U;
     int c0 = (2 * j + a.ox) % U;
-    float r0 = 0.f, r1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int x = 2 * (j + q * T);
-      const float g0 = v[q].x * a.inv_n3, g1 = v[q].y * a.inv_n3;
-      const int c1 = c0 + 1 == U ? 0 : c0 + 1;
-      if (drow) *reinterpret_cast<float2*>(drow + x) = make_float2(g0 * __ldg(crow + c0), g1 * __ldg(crow + c1));
-      float m0, m1;
-      if (wrow) {
-        const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
-        m0 = mw.x;
-        m1 = mw.y;
-      } else {
-        m0 = rm.at(x);
-        m1 = rm.at(x + 1);
-      }
-      if (cstep == 0) {
-        r0 += g0 * m0;
-        r1 += g1 * m1;
-      } else {
-        if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
-        if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
-      }
-      c0 += cstep;
-      if (c0 >= U) c0 -= U;
-    }
     if (cstep == 0) {
+      const int c1 = c0 + 1 == U ? 0 : c0 + 1;
+      const float u0 = __ldg(crow + c0), u1 = __ldg(crow + c1);
+      float r0 = 0.f, r1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int x = 2 * (j + q * T);
+        const float g0 = v[q].x * a.inv_n3, g1 = v[q].y * a.inv_n3;
+        if (drow) *reinterpret_cast<float2*>(drow + x) = make_float2(g0 * u0, g1 * u1);
+        if (!mzero) {
+          float m0, m1;
+          if (wrow) {
+            const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+            m0 = mw.x;
+            m1 = mw.y;
+          } else {
+            m0 = rm.at(x);
+            m1 = rm.at(x + 1);
+          }
+          r0 += g0 * m0;
+          r1 += g1 * m1;
+        }
+      }
       if (r0 != 0.f) atomicAdd(acc + c0, r0);
-      if (r1 != 0.f) atomicAdd(acc + (c0 + 1 == U ? 0 : c0 + 1), r1);
+      if (r1 != 0.f) atomicAdd(acc + c1, r1);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int x = 2 * (j + q * T);
+        const float g0 = v[q].x * a.inv_n3, g1 = v[q].y * a.inv_n3;
+        const int c1 = c0 + 1 == U ? 0 : c0 + 1;
+        if (drow) *reinterpret_cast<float2*>(drow + x) = make_float2(g0 * __ldg(crow + c0), g1 * __ldg(crow + c1));
+        if (!mzero) {
+          float m0, m1;
+          if (wrow) {
+            const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+            m0 = mw.x;
+            m1 = mw.y;
+          } else {
+            m0 = rm.at(x);
+            m1 = rm.at(x + 1);
+          }
+          if (m0 != 0.f) atomicAdd(acc + c0, g0 * m0);
+          if (m1 != 0.f) atomicAdd(acc + c1, g1 * m1);
+        }
+        c0 += cstep;
+        if (c0 >= U) c0 -= U;
+      }
     }
   }
   __syncthreads();

@@ -124,7 +124,6 @@ __device__ __forceinline__ void load_columns(const ColArgs& a, float2* buf, long
     float2 v = make_float2(0.f, 0.f);
     if (c < a.ncols && li >= 0 && li < a.nload) {
       v = __ldg(a.src + col_offset(c, a.H, a.A) + (long long)li * a.S);
-      if (a.fin_mul != 1.f) v = cscale(v, a.fin_mul);
     }
     buf[t * a.pitch + i] = v;
   }
@@ -571,7 +570,6 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.thr = p->thr;
   a.lut = p->binlut;
   a.nbins = p->nbins;
-  a.fin_mul = 1.f;
   return a;
 }
 

@@ -37,7 +37,6 @@ struct ColArgs {
   float fscale;
   // adjoint
   const float* sigma;  // per-bin scale of F~ along z (adjoint)
-  float fin_mul;       // multiplier applied to every loaded element
   int skip_fwd;        // 1: the loaded column is already the spectrum along z
 };
 
