@@ -436,7 +436,16 @@ __global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
   for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
   float2* line = sm + t * PITCH;
   const float2* Yrow = a.Y + ((long long)(z - a.ybase_z) * N + (valid ? y : 0)) * H;
-  for (int k = j; k < H; k += T) line[p2pad(k)] = valid ? __ldg(Yrow + k) : make_float2(0.f, 0.f);
+  {
+    // all nine loads of the row (k = j + q T, and k = M) are issued before any is stored
+    float2 ld[9];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ld[q] = valid ? __ldg(Yrow + j + q * T) : make_float2(0.f, 0.f);
+    ld[8] = (valid && j == 0) ? __ldg(Yrow + M) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = ld[q];
+    if (j == 0) line[p2pad(M)] = ld[8];
+  }
   __syncthreads();  // also orders the zeroing of acc before any accumulation
   float2 v[8];
 #pragma unroll
