@@ -123,6 +123,18 @@ size_t ur_workspace_size(const ur_plan* plan, int32_t what);
  * 256 MiB of ED per slab).  Changes ur_workspace_size(plan, UR_WS_HOST_SLABS). */
 ur_status ur_plan_set_slab_planes(ur_plan* plan, int32_t planes);
 
+/* Planes per chunk of the power-of-two path.  With chunks, the row pass and the
+ * y-column pass of one chunk of planes run back to back so that the chunk's
+ * intermediate is re-read from L2, and the adjoint's y-inverse of a chunk goes
+ * to a chunk buffer that its row pass reads from L2.  Default: N (every pass is
+ * one launch over all planes and the adjoint's y-inverse runs in place; no
+ * chunk buffer).  planes >= 1 (clamped to N).  Changes ur_workspace_size(plan,
+ * UR_WS_BACKWARD); results do not depend on it beyond rounding order.
+ * ur_plan_chunk_planes returns the current value (0 for the runtime-radix path,
+ * which does not chunk). */
+ur_status ur_plan_set_chunk_planes(ur_plan* plan, int32_t planes);
+int32_t ur_plan_chunk_planes(const ur_plan* plan);
+
 /* ---------------------------------------------------------------------------
  * ur_build_density (Sec. 2.3).
  * ------------------------------------------------------------------------- */

@@ -70,6 +70,8 @@ SIGNATURES = {
     "ur_batch_forward": (_i32, [_vp, _vp]),
     "ur_batch_backward": (_i32, [_vp, _vp]),
     "ur_plan_set_tiles": (_i32, [_vp, _i32, _i32]),
+    "ur_plan_set_chunk_planes": (_i32, [_vp, _i32]),
+    "ur_plan_chunk_planes": (_i32, [_vp]),
     "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
 # test hooks (not part of the header's API)
@@ -182,6 +184,12 @@ class Plan:
 
     def set_slab_planes(self, planes: int):
         _check("ur_plan_set_slab_planes", lib().ur_plan_set_slab_planes(self._h, int(planes)))
+
+    def set_chunk_planes(self, planes: int):
+        _check("ur_plan_set_chunk_planes", lib().ur_plan_set_chunk_planes(self._h, int(planes)))
+
+    def chunk_planes(self) -> int:
+        return int(lib().ur_plan_chunk_planes(self._h))
 
     def workspace(self, what: int = UR_WS_FORWARD, device="cuda") -> torch.Tensor:
         return torch.empty(self.workspace_size(what), dtype=torch.uint8, device=device)

@@ -195,9 +195,11 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
   ur_timing_end(s);
 
   if (p->fast) {
-    // B2 + B3 in plane chunks: the y-inverse of a chunk goes to a chunk buffer
-    // that stays in L2 until the row pass of the same chunk has read it.
+    // B2 + B3, over all planes with the y-inverse in place, or in plane chunks
+    // whose y-inverse goes to a chunk buffer that the row pass of the same chunk
+    // reads while it is still in L2.
     UR_REQUIRE(!weights || ((uintptr_t)weights % 8) == 0, "ur_backward: weights must be 8-byte aligned");
+    const bool whole = p->chunk_planes >= n;
     float2* C = (float2*)((char*)sigma + ur_align_up(p->ws_sigma, 256));
     GradArgs g;
     memset(&g, 0, sizeof g);
@@ -219,7 +221,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
       const int np = (p0 + p->chunk_planes <= n) ? p->chunk_planes : n - p0;
       ColArgs b = ur_col_args(p);
       b.src = Y + (long long)p0 * n * H;
-      b.dst = C;
+      b.dst = whole ? Y : C;
       b.ncols = (long long)np * H;
       b.A = (long long)n * H;
       b.S = H;
@@ -231,7 +233,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
       ur_timing_begin("adj_cols_y", s);
       UR_TRY(ur_fast_cols(n, 1 /* y inverse */, b, s));
       ur_timing_end(s);
-      g.Y = C;
+      g.Y = whole ? Y : C;
       g.ybase_z = p0;
       g.z0 = p0;
       ur_timing_begin("adj_rows_grad", s);

@@ -436,8 +436,8 @@ struct ur_plan {
   int slab_planes;
   // power-of-two path
   int fast;          // 1: compile-time kernels (N a power of two in [64, 1024])
-  int chunk_planes;  // planes per L2-resident chunk of the plane pass / adjoint rows
-  size_t ws_chunk;   // adjoint chunk buffer
+  int chunk_planes;  // planes per chunk of the plane pass / adjoint y and row passes (n: one launch each)
+  size_t ws_chunk;   // adjoint chunk buffer (0 when chunk_planes = n: y-inverse in place)
 };
 
 // kernels launched from host code in other translation units

@@ -23,8 +23,6 @@
 #include "ur_density.cuh"
 #include "ur_fast.cuh"
 
-#define BIN_CHUNK_F 8
-
 template <int L>
 struct P2 {
   static constexpr int LOG = L == 8 ? 3 : L == 16 ? 4 : L == 32 ? 5 : L == 64 ? 6 : L == 128 ? 7 : L == 256 ? 8
@@ -38,15 +36,6 @@ struct P2 {
 };
 
 __device__ __forceinline__ int p2pad(int i) { return i + (i >> 4); }
-
-// smallest r >= 0 with r*r >= v, for 0 <= v < 2^24 (float sqrt is within one of it)
-__device__ __forceinline__ int isqrt_ceil(int v) {
-  if (v <= 0) return 0;
-  int r = (int)sqrtf((float)v);
-  while (r * r < v) ++r;
-  while (r > 0 && (r - 1) * (r - 1) >= v) --r;
-  return r;
-}
 
 constexpr int ipow8(int s) { return s == 0 ? 1 : 8 * ipow8(s - 1); }
 
@@ -332,58 +321,70 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       for (int q = 0; q < 8; ++q) a.fout[(long long)(j + q * T) * N * H + col] = cscale(v[q], a.fscale);
     }
     if (binning) {
-      // natural order in shared memory, then contiguous |kz| chunks per thread
+      // task = (column, chunk of CH consecutive |kz| = m); at most one task per thread.
+      // The bin of the chunk's first m comes from the k^2 table (its load is issued
+      // before the barrier below); after that the bin only moves forward, when
+      // s = c2 + m^2 (updated by 2m + 1) reaches the next threshold, so the loop over
+      // the chunk compares, accumulates a run of equal bins and flushes it on a change.
+      constexpr int CH = (H + T - 1) / T;
+      constexpr int NCH = (H + CH - 1) / CH;
+      static_assert(TX * NCH <= ColCfg<N>::THREADS, "one binning task per thread");
+      const int nb = a.nbins;
+      const int tc = threadIdx.x % TX, ch = threadIdx.x / TX;
+      const int gcol = col0 + tc;
+      const bool has = ch < NCH && gcol < a.ncols;
+      int cc2 = 0, m0 = 0, bcur = 0;
+      float w = 0.f;
+      if (has) {
+        const int o2 = gcol / H, kx2 = gcol - o2 * H, ky2 = o2 < M ? o2 : o2 - N;
+        cc2 = kx2 * kx2 + ky2 * ky2;
+        w = (kx2 == 0 || kx2 == M) ? 1.f : 2.f;
+        m0 = ch * CH;
+        const int s0 = cc2 + m0 * m0;
+        bcur = s0 < thr[0] ? -1 : s0 >= thr[nb] ? nb : __ldg(a.lut + s0);
+      }
+      // natural order in shared memory
 #pragma unroll
       for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
       __syncthreads();
-      // task = (column, chunk of CH consecutive |kz| = m); one task per thread at most.
-      // Inside a chunk the bin changes only where c2 + m^2 crosses the next threshold,
-      // found from the threshold itself (integer square root), so the inner loop over a
-      // run of equal bins only loads and accumulates.
-      constexpr int CH = (H + T - 1) / T;
-      constexpr int NCH = (H + CH - 1) / CH;
-      const int nb = a.nbins;
-      for (int task = threadIdx.x; task < TX * NCH; task += blockDim.x) {
-        const int tc = task % TX, ch = task / TX;
-        const int gcol = col0 + tc;
-        if (gcol >= a.ncols) continue;
-        const int o = gcol / H, kx2 = gcol - o * H, ky2 = o < M ? o : o - N;
-        const int cc2 = kx2 * kx2 + ky2 * ky2;
-        const float w = (kx2 == 0 || kx2 == M) ? 1.f : 2.f;
+      if (has) {
         const float2* ln = buf + tc * PITCH;
-        const int m1 = min(ch * CH + CH, M + 1);
-        int m = ch * CH;
-        while (m < m1) {
-          const int s = cc2 + m * m;
-          int b = -1, mend;
-          if (s < thr[0]) {
-            mend = isqrt_ceil(thr[0] - cc2);
-          } else if (s >= thr[nb]) {
-            mend = m1;
-          } else {
-            b = __ldg(a.lut + s);
-            mend = isqrt_ceil(thr[b + 1] - cc2);
-          }
-          if (mend > m1) mend = m1;
-          if (mend <= m) mend = m + 1;
-          if (b >= 0) {
-            float sI = 0.f, sI2 = 0.f;
-            for (int mm = m; mm < mend; ++mm) {
-              const float2 f1 = ln[p2pad(mm)];
-              const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
-              sI += i1;
-              sI2 += i1 * i1;
-              if (mm != 0 && mm != M) {
-                const float2 f2 = ln[p2pad(N - mm)];
-                const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
-                sI += i2;
-                sI2 += i2 * i2;
+        int b = bcur;
+        int tnext = b < nb ? thr[b + 1] : 0x7fffffff;
+        int s = cc2 + m0 * m0;
+        float sI = 0.f, sI2 = 0.f;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int mm = m0 + u;
+          if (mm <= M) {
+            if (s >= tnext) {
+              if (b >= 0) {
+                atomicAdd(hs + b, w * sI);
+                atomicAdd(hs2 + b, w * sI2);
               }
+              sI = 0.f;
+              sI2 = 0.f;
+              do {
+                ++b;
+                tnext = b < nb ? thr[b + 1] : 0x7fffffff;
+              } while (s >= tnext);
             }
-            atomicAdd(hs + b, w * sI);
-            atomicAdd(hs2 + b, w * sI2);
+            const float2 f1 = ln[p2pad(mm)];
+            const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
+            sI += i1;
+            sI2 += i1 * i1;
+            if (mm != 0 && mm != M) {
+              const float2 f2 = ln[p2pad(N - mm)];
+              const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
+              sI += i2;
+              sI2 += i2 * i2;
+            }
+            s += 2 * mm + 1;
           }
-          m = mend;
+        }
+        if (b >= 0 && b < nb) {
+          atomicAdd(hs + b, w * sI);
+          atomicAdd(hs2 + b, w * sI2);
         }
       }
       __syncthreads();

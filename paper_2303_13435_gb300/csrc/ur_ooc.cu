@@ -20,6 +20,18 @@ extern "C" ur_status ur_plan_set_slab_planes(ur_plan* p, int32_t planes) {
   return UR_OK;
 }
 
+extern "C" ur_status ur_plan_set_chunk_planes(ur_plan* p, int32_t planes) {
+  UR_REQUIRE(p && planes >= 1, "ur_plan_set_chunk_planes: bad argument");
+  if (!p->fast) return UR_OK;
+  const size_t plane_bytes = (size_t)p->n * p->H * sizeof(float2);
+  p->chunk_planes = planes > p->n ? p->n : planes;
+  // whole-grid passes transform Y in place; chunks need their own buffer
+  p->ws_chunk = p->chunk_planes < p->n ? (size_t)p->chunk_planes * plane_bytes : 0;
+  return UR_OK;
+}
+
+extern "C" int32_t ur_plan_chunk_planes(const ur_plan* p) { return (p && p->fast) ? p->chunk_planes : 0; }
+
 ur_status ur_fft_intensity_host(const ur_plan* p, const void* ed_host, double* bins, float2* F_out, void* ws,
                                 size_t ws_bytes, cudaStream_t s) {
   const size_t need = ur_workspace_size(p, UR_WS_FORWARD | UR_WS_HOST_SLABS);

@@ -318,7 +318,7 @@ def test_n1024_sampled_F_parseval_and_counts():
     assert int(gb[0].sum()) == n ** 3
 
 
-@pytest.mark.parametrize("case", ["mof128_weights_origin", "mof256_chunks", "sc64_tiled"])
+@pytest.mark.parametrize("case", ["mof128_weights_origin", "mof256_chunks", "mof256_chunk7", "sc64_tiled"])
 def test_backward_fast_path(case):
     weights = None
     if case == "mof128_weights_origin":
@@ -327,17 +327,24 @@ def test_backward_fast_path(case):
         weights[:30] = 0
         weights[98:] = 0
         w.shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
-    elif case == "mof256_chunks":
+    elif case in ("mof256_chunks", "mof256_chunk7"):
         w = mof(256, 110, kind=inputs.SHAPE_CUBE, rot_seed=3)
     else:
         w = inputs.sc64_workload()
     rho = oracle_density(w, weights=weights)
     z0, nz = z_range(rho)
     plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    if case == "mof256_chunk7":
+        # 7-plane chunks: the plane pass and the adjoint's chunk loop end on a ragged chunk
+        plan.set_chunk_planes(7)
+        assert plan.chunk_planes() == 7 and nz % 7 != 0 and 256 % 7 != 0
     ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
     wd = dev(weights) if weights is not None else None
     bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, origin=w.origin, weights=wd, ws=ws)
     gb = bins.cpu().numpy()
+    if case == "mof256_chunk7":
+        r64 = rho.astype(np.float64)
+        compare_bins(gb, oracle_forward(r64, w.dx, w.edges), r64, case)
     g = np.where(gb[0] > 0, 1.0 / np.maximum(np.nan_to_num(gb[4]), 1e-300), 0.0) * 1e-3
     dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws, origin=w.origin, weights=wd)
     mask = density.mask_values(w.n, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot, weights)
