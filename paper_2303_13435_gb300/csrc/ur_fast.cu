@@ -265,14 +265,6 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   const int col = col0 + c;
   const bool valid = col < a.ncols;
   const bool binning = (MODE == P2_Z_BIN || MODE == P2_Z_ADJ) && a.nbins > 0;
-  if (MODE == P2_Z_BIN && binning) {
-    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
-    if (MODE == P2_Z_BIN && threadIdx.x == 0) {
-      s_blo = 0x7fffffff;
-      s_bhi = -1;
-    }
-    __syncthreads();
-  }
   // column position of the spectrum (z passes): kx, ky
   int kx = 0, ky = 0;
   {
@@ -281,15 +273,22 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     ky = o < M ? o : o - N;
   }
   const int c2 = kx * kx + ky * ky;
+  // z pass with binning: the bins a column can reach lie between those of k^2 = c2
+  // and c2 + M^2 (clamped to the bin range); their table loads are issued here and
+  // used after the column loads, and the block's histogram range [s_blo, s_bhi] is
+  // zeroed after the transform (whose barriers order it after the updates below)
+  int lo_bin = 0, hi_bin = 0;
   if (MODE == P2_Z_BIN && binning) {
-    if (j == 0 && valid) {
-      atomicMin(&s_blo, max(bin_search(thr, a.nbins, c2), 0));
-      atomicMax(&s_bhi, min(bin_search(thr, a.nbins, c2 + M * M), a.nbins - 1));
+    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
+    if (threadIdx.x == 0) {
+      s_blo = 0x7fffffff;
+      s_bhi = -1;
     }
-    __syncthreads();
-    for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
-      hs[i] = 0.f;
-      hs2[i] = 0.f;
+    if (j == 0 && valid) {
+      const int nb = a.nbins, t0 = __ldg(a.thr), tn = __ldg(a.thr + nb);
+      const int s_lo = c2, s_hi = c2 + M * M;
+      lo_bin = s_lo < t0 ? 0 : s_lo >= tn ? nb - 1 : __ldg(a.lut + s_lo);
+      hi_bin = s_hi < t0 ? 0 : s_hi >= tn ? nb - 1 : __ldg(a.lut + s_hi);
     }
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
@@ -307,6 +306,13 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     }
   }
   float2* line = buf + c * PITCH;
+  if (MODE == P2_Z_BIN && binning) {
+    __syncthreads();  // thr and the range reset are visible
+    if (j == 0 && valid) {
+      atomicMin(&s_blo, lo_bin);
+      atomicMax(&s_bhi, hi_bin);
+    }
+  }
   if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
     p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.tw, 1);
     if (valid) {
@@ -342,6 +348,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
         m0 = ch * CH;
         const int s0 = cc2 + m0 * m0;
         bcur = s0 < thr[0] ? -1 : s0 >= thr[nb] ? nb : __ldg(a.lut + s0);
+      }
+      for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
+        hs[i] = 0.f;
+        hs2[i] = 0.f;
       }
       // natural order in shared memory
 #pragma unroll
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
 //   z = IFFT_{N/2}(Z),  (g(2m), g(2m+1)) = (Re z[m], Im z[m]).
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(512) k_p2_rows_grad(GradArgs a) {
+__global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
   constexpr int M = N / 2, H = M + 1, T = M / 8, PITCH = P2<M>::PITCH + 1;
   constexpr bool WS = T <= 32;
   extern __shared__ __align__(16) unsigned char smraw[];
