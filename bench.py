@@ -53,6 +53,49 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# library kernel behind each timing label of the step (for the ncu profile lookup)
+KERNEL_OF = {
+    "rows_r2c": "k_p2_rows<512, 1, float>",
+    "cols_y": "k_p2_cols<512, 0>",
+    "cols_z_bin": "k_p2_cols<512, 2>",
+    "adj_cols_z": "k_p2_cols<512, 3>",
+    "adj_cols_y": "k_p2_cols<512, 1>",
+    "adj_rows_grad": "k_p2_rows_grad<512>",
+}
+
+
+def csrc_digest() -> str:
+    """sha256 over the CUDA sources; a profile taken from other sources is stale."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2303_13435_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu summary
+    under profiles/ taken on the current sources, else None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None, None
+    digest = csrc_digest()
+    for f in sorted(os.listdir(pdir)):
+        if not f.endswith(".txt"):
+            continue
+        kv = {}
+        for line in open(os.path.join(pdir, f)):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel") == kernel and kv.get("source_sha256") == digest and "traffic_bytes_per_launch" in kv:
+            return float(kv["traffic_bytes_per_launch"]), f"profiles/{f}"
+    return None, None
+
+
 def workload(n: int):
     from paper_2303_13435_gb300 import inputs
     d = 10.0 * n / 512.0
@@ -251,11 +294,19 @@ def run_ours(args):
                    "gbs": (kb.get(k, 0) * args.steps / (ms * 1e-3) / 1e9) if kb.get(k, 0) else None}
                for k, (ms, c) in per.items()}
     # step-level algorithmic bytes: forward 16 N H P (intermediate written and read once; the
-    # density is generated, not read) + adjoint
+    # density is generated, not read) + adjoint 8 N H P (read the forward intermediate) +
+    # 16 N^2 H (the inverse intermediate of all N planes written and read once) + 4 N^3 (dL/dm)
     H = n // 2 + 1
     fwd_alg = 16 * n * H * P
-    adj_alg = 8 * n * H * P + 24 * n * n * H + 4 * n ** 3
+    adj_alg = 8 * n * H * P + 16 * n * n * H + 4 * n ** 3
     step_frac = (fwd_alg + adj_alg) / (ms_step * 1e-3) / 1e9 / hbm
+    # forward gate: e N^2 P + 16 N H P (stored FP32 ED read + intermediate written and read)
+    # over the forward kernels' time
+    fwd_names = ("rows_r2c", "cols_y", "cols_z_bin", "finalize")
+    fwd_ms = sum(per[k][0] for k in fwd_names if k in per) / args.steps
+    fwd_gate_bytes = 4 * n * n * P + 16 * n * H * P
+    fwd_frac = fwd_gate_bytes / (fwd_ms * 1e-3) / 1e9 / hbm
+    traffic, traffic_src = profiled_traffic(KERNEL_OF.get(dom_name, ""))
 
     # end to end through the public API with host buffers
     cell_host = torch.from_numpy(w.cell).pin_memory()
@@ -301,9 +352,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (ED slab, intermediates); no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                     else "fallback 6800 GB/s", "traffic": None,
-                     "step_frac_of_hbm": step_frac},
+                     "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+                     if src == "measured" else "fallback 6800 GB/s", "traffic": traffic,
+                     "traffic_source": traffic_src, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "step_frac_of_hbm": step_frac,
+                     "forward": {"us_per_step": 1e3 * fwd_ms, "gate_bytes": fwd_gate_bytes, "frac": fwd_frac}},
         "kernels": kernels,
         "timing": {"value_from": "CUDA-graph replays of the step", "ms_per_step_eager": ms_eager,
                    "kernel_times_from": "library events around each launch, eager pass of the same steps"},
