@@ -189,7 +189,10 @@ ur_status ur_fft_intensity(const ur_plan* plan, const void* ed, int32_t ed_on_ho
  * (Sec. 2.3 tile + mask fused with Sec. 2.4): the ED of planes
  * [z0, z0+nz) is never stored.  cell, ucell, origin, shape and weights are
  * as for ur_build_density; the transform sees exactly the values
- * ur_build_density would write (FP32).  The plan's ed_dtype is ignored. */
+ * ur_build_density would write (FP32).  The plan's ed_dtype is ignored.
+ * Cell values must be finite: a row whose mask is zero everywhere (a sphere
+ * row outside the particle, or any row whose generated values are all zero)
+ * is taken as zero without evaluating u * 0. */
 ur_status ur_fft_intensity_tiled(const ur_plan* plan, const float* cell, int32_t ucell, const int32_t* origin,
                                  const ur_shape* shape, const float* weights, double* bins, void* F_out, void* ws,
                                  size_t ws_bytes, void* stream);
