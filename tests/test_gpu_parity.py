@@ -357,23 +357,26 @@ def test_backward_fast_path(case):
     assert eu <= GRAD_RTOL and em <= GRAD_RTOL
 
 
-def test_mof512_full_size_forward_and_adjoint():
-    """The 512^3 workload of the benchmark, in its launch configuration (fused tiled
-    forward, recomputing adjoint), against the FP64 oracle."""
+@pytest.mark.parametrize("keep_f", [True, False])
+def test_mof512_full_size_forward_and_adjoint(keep_f):
+    """The 512^3 workload of the benchmark against the FP64 oracle: fused tiled forward,
+    then the adjoint from the kept half spectrum F (the benchmark's launch configuration)
+    or recomputing F along z from the plane-pass intermediate."""
     w = inputs.mof_workload(n=512, diameter_nm=10.0, nbins=512)
     rho = oracle_density(w)
     z0, nz = z_range(rho)
     assert nz == 247
     plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
     ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
-    bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, ws=ws)
+    Fh = torch.empty((512, 512, 257, 2), device="cuda") if keep_f else None
+    bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, ws=ws, F_out=Fh)
     gb = bins.cpu().numpy()
     r64 = rho.astype(np.float64)
     ob = oracle_forward(r64, w.dx, w.edges)
     rep = compare_bins(gb, ob, r64, "mof512")
     print("mof512 forward", rep)
     g = np.where(gb[0] > 0, 1.0 / np.maximum(np.nan_to_num(gb[4]), 1e-300), 0.0) * 1e-3
-    dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws)
+    dcell, dmask = api.backward(plan, dev(g), bins, dev(w.cell), w.shape, ws, F=Fh)
     mask = density.mask_values(w.n, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot)
     gu, gm = oracle_grads(r64, w.cell.astype(np.float64), mask, w.dx, w.edges, g, ob["count"])
     eu = normwise(dcell.cpu().numpy(), gu)
