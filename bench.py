@@ -77,9 +77,9 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(kernel: str):
+def profiled_traffic(kernel: str, variant: str):
     """DRAM bytes (read + write) per launch of `kernel` from a committed ncu summary
-    under profiles/ taken on the current sources, else None."""
+    under profiles/ taken on the current sources in the same launch variant, else None."""
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None, None
@@ -92,7 +92,8 @@ def profiled_traffic(kernel: str):
             if ":" in line:
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel") == kernel and kv.get("source_sha256") == digest and "traffic_bytes_per_launch" in kv:
+        if (kv.get("kernel") == kernel and kv.get("variant") == variant and kv.get("source_sha256") == digest
+                and "traffic_bytes_per_launch" in kv):
             return float(kv["traffic_bytes_per_launch"]), f"profiles/{f}"
     return None, None
 
@@ -311,7 +312,7 @@ def run_ours(args):
     fwd_ms = sum(per[k][0] for k in fwd_names if k in per) / args.steps
     fwd_gate_bytes = 4 * n * n * P + 16 * n * H * P
     fwd_frac = fwd_gate_bytes / (fwd_ms * 1e-3) / 1e9 / hbm
-    traffic, traffic_src = profiled_traffic(KERNEL_OF.get(dom_name, ""))
+    traffic, traffic_src = profiled_traffic(KERNEL_OF.get(dom_name, ""), "keepF")
 
     # end to end through the public API with host buffers
     cell_host = torch.from_numpy(w.cell).pin_memory()
