@@ -408,6 +408,18 @@ __device__ __forceinline__ int bin_search(const int32_t* __restrict__ thr, int n
   return lo - 1;
 }
 
+// Rank of k^2 = s among the bin thresholds, r(s) = max{j in [0, nb] : thr[j] <= s}
+// (-1 below thr[0]); s lies in bin r when 0 <= r < nb.  crs holds r at multiples of
+// 2^shift, so the rank of s is reached from crs[s >> shift] by stepping over the few
+// thresholds inside that block.  The two tables are small (6 KB and 4 (nb+1) bytes),
+// so a kernel that needs the bin of every element keeps them in shared memory.
+#define UR_COARSE_ENTRIES 3072
+__device__ __forceinline__ int bin_rank(const int16_t* crs, int shift, const int32_t* thr, int nb, int s) {
+  int b = crs[s >> shift];
+  while (b < nb && thr[b + 1] <= s) ++b;
+  return b;
+}
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
@@ -418,7 +430,9 @@ struct ur_plan {
   int device, num_sms;
   float2* tw;        // device [n]
   int32_t* thr;      // device [nbins+1]
-  int16_t* binlut;   // device [3 (N/2)^2 + 1]: bin of k^2 = s, -1 outside every bin
+  int16_t* binlut;     // device [3 (N/2)^2 + 1]: bin of k^2 = s, -1 outside every bin
+  int16_t* bincoarse;  // device [UR_COARSE_ENTRIES]: bin_rank of s = i << coarse_shift
+  int coarse_shift;    // smallest shift with (3 (N/2)^2 >> shift) < UR_COARSE_ENTRIES
   int64_t* thr_host; // host   [nbins+1]
   double* geo;       // device [2][nbins]: count, sum |Q|
   Sched sched_n, sched_m;       // host copies

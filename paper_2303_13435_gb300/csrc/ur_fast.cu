@@ -226,18 +226,6 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
 // ---------------------------------------------------------------------------
 enum { P2_Y_FWD = 0, P2_Y_INV = 1, P2_Z_BIN = 2, P2_Z_ADJ = 3 };
 
-// bins of the 8 values of thread j (kz = j + qT), from the k^2 -> bin table
-template <int N>
-__device__ __forceinline__ void p2_bins8(int c2, int j, const int16_t* __restrict__ lut, int (&bin)[8]) {
-  constexpr int T = N / 8;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int kz = j + q * T;
-    const int m = kz <= N / 2 ? kz : N - kz;
-    bin[q] = __ldg(lut + c2 + m * m);
-  }
-}
-
 // threads per column block: 512, or 1024 for N >= 2048 so that a block still
 // spans at least two columns (16-byte row segments) of the half spectrum
 // MINB: resident blocks per SM the register budget is cut for (the z pass
@@ -260,6 +248,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   int32_t* thr = reinterpret_cast<int32_t*>(smraw + BUF_BYTES);
   float* hs = reinterpret_cast<float*>(smraw + BUF_BYTES + ur_align_up_dev((size_t)(a.nbins + 1) * 4, 16));
   float* hs2 = hs + a.nbins;
+  int16_t* crs = reinterpret_cast<int16_t*>(reinterpret_cast<unsigned char*>(hs) +
+                                            ur_align_up_dev((size_t)a.nbins * 8, 16));  // 16-byte aligned
   const int c = threadIdx.x % TX, j = threadIdx.x / TX;
   const int col0 = blockIdx.x * TX;
   const int col = col0 + c;
@@ -273,22 +263,30 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     ky = o < M ? o : o - N;
   }
   const int c2 = kx * kx + ky * ky;
-  // z pass with binning: the bins a column can reach lie between those of k^2 = c2
-  // and c2 + M^2 (clamped to the bin range); their table loads are issued here and
-  // used after the column loads, and the block's histogram range [s_blo, s_bhi] is
-  // zeroed after the transform (whose barriers order it after the updates below)
+  // z passes: the bin thresholds go to shared memory.  The adjoint, which needs the bin
+  // of every element, also stages the coarse rank table and its per-bin scales there (no
+  // gathers from global memory per element).  The forward binning needs only a few bins
+  // per column: the bins a column can reach lie between those of k^2 = c2 and c2 + M^2,
+  // read here from the full k^2 -> bin table and used after the column loads.
   int lo_bin = 0, hi_bin = 0;
-  if (MODE == P2_Z_BIN && binning) {
+  if (binning) {
     for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
-    if (threadIdx.x == 0) {
-      s_blo = 0x7fffffff;
-      s_bhi = -1;
+    if (MODE == P2_Z_ADJ) {
+      for (int i = threadIdx.x; i < UR_COARSE_ENTRIES / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(crs)[i] = __ldg(reinterpret_cast<const uint4*>(a.crs) + i);
+      for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) hs[i] = __ldg(a.sigma + i);
     }
-    if (j == 0 && valid) {
-      const int nb = a.nbins, t0 = __ldg(a.thr), tn = __ldg(a.thr + nb);
-      const int s_lo = c2, s_hi = c2 + M * M;
-      lo_bin = s_lo < t0 ? 0 : s_lo >= tn ? nb - 1 : __ldg(a.lut + s_lo);
-      hi_bin = s_hi < t0 ? 0 : s_hi >= tn ? nb - 1 : __ldg(a.lut + s_hi);
+    if (MODE == P2_Z_BIN) {
+      if (threadIdx.x == 0) {
+        s_blo = 0x7fffffff;
+        s_bhi = -1;
+      }
+      if (j == 0 && valid) {
+        const int nb = a.nbins, t0 = __ldg(a.thr), tn = __ldg(a.thr + nb);
+        const int s_lo = c2, s_hi = c2 + M * M;
+        lo_bin = s_lo < t0 ? 0 : s_lo >= tn ? nb - 1 : __ldg(a.lut + s_lo);
+        hi_bin = s_hi < t0 ? 0 : s_hi >= tn ? nb - 1 : __ldg(a.lut + s_hi);
+      }
     }
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
@@ -306,12 +304,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     }
   }
   float2* line = buf + c * PITCH;
-  if (MODE == P2_Z_BIN && binning) {
-    __syncthreads();  // thr and the range reset are visible
-    if (j == 0 && valid) {
-      atomicMin(&s_blo, lo_bin);
-      atomicMax(&s_bhi, hi_bin);
-    }
+  if (binning) __syncthreads();  // tables (and the histogram range reset) visible
+  if (MODE == P2_Z_BIN && binning && j == 0 && valid) {
+    // the block's histogram range [s_blo, s_bhi] is zeroed after the transform, whose
+    // barriers order it after these updates
+    atomicMin(&s_blo, lo_bin);
+    atomicMax(&s_bhi, hi_bin);
   }
   if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
     p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.tw, 1);
@@ -405,12 +403,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     }
   } else {  // P2_Z_ADJ
     if (!a.skip_fwd) p2_fft<N, false>(v, j, line, a.tw, 1);
-    int bin[8];
-    p2_bins8<N>(c2, j, a.lut, bin);
+    // scale of element kz: sigma of the bin of k^2 = c2 + m^2, m = |signed kz|
+    const int nb = a.nbins;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float sg = (bin[q] >= 0 && bin[q] < a.nbins) ? __ldg(a.sigma + bin[q]) : 0.f;
-      v[q] = cscale(v[q], sg);
+      const int kz = j + q * T;
+      const int m = kz <= M ? kz : N - kz;
+      const int b = bin_rank(crs, a.crs_shift, thr, nb, c2 + m * m);
+      v[q] = cscale(v[q], (b >= 0 && b < nb) ? hs[b] : 0.f);
     }
     p2_fft<N, true>(v, j, line, a.tw, 1);
     if (valid) {
@@ -546,16 +546,16 @@ bool ur_fast_supported(int n) {
 }
 
 template <int N>
-static size_t cols_smem(int nbins) {
+static size_t cols_smem(int nbins, int mode) {
   constexpr int TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2;
   return ur_align_up((size_t)TX * PITCH * sizeof(float2), 16) + ur_align_up((size_t)(nbins + 1) * 4, 16) +
-         (size_t)nbins * 8;
+         ur_align_up((size_t)nbins * 8, 16) + (mode == P2_Z_ADJ ? (size_t)UR_COARSE_ENTRIES * 2 : 0);
 }
 
 template <int N>
 static ur_status launch_cols_n(int mode, const ColArgs& a, cudaStream_t s) {
   constexpr int TX = ColCfg<N>::TX;
-  const size_t smem = cols_smem<N>(a.nbins);
+  const size_t smem = cols_smem<N>(a.nbins, mode);
   const int grid = (int)((a.ncols + TX - 1) / TX);
   if (grid <= 0) return UR_OK;
 #define UR_P2_LAUNCH(MD)                                                                                   \

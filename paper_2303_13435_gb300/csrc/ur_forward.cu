@@ -413,12 +413,23 @@ __global__ void k_binlut(const int32_t* __restrict__ thr, int nb, int smax, int1
   lut[s] = (int16_t)((b >= 0 && b < nb) ? b : -1);
 }
 
+__global__ void k_bincoarse(const int32_t* __restrict__ thr, int nb, int shift, int16_t* __restrict__ crs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < UR_COARSE_ENTRIES) crs[i] = (int16_t)bin_search(thr, nb, i << shift);
+}
+
 ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s) {
   {
     const int smax = 3 * (p->n / 2) * (p->n / 2);
+    int sh = 0;
+    while ((smax >> sh) >= UR_COARSE_ENTRIES) ++sh;
+    p->coarse_shift = sh;
     UR_CUDA_CHECK(cudaMalloc(&p->binlut, sizeof(int16_t) * ((size_t)smax + 1)));
     k_binlut<<<(smax + 256) / 256, 256, 0, s>>>(p->thr, p->nbins, smax, p->binlut);
     UR_LAUNCH_CHECK("k_binlut");
+    UR_CUDA_CHECK(cudaMalloc(&p->bincoarse, sizeof(int16_t) * UR_COARSE_ENTRIES));
+    k_bincoarse<<<(UR_COARSE_ENTRIES + 255) / 256, 256, 0, s>>>(p->thr, p->nbins, sh, p->bincoarse);
+    UR_LAUNCH_CHECK("k_bincoarse");
   }
   const int nb = p->nbins;
   unsigned long long* cnt = nullptr;
@@ -567,6 +578,8 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.tw = p->tw;
   a.thr = p->thr;
   a.lut = p->binlut;
+  a.crs = p->bincoarse;
+  a.crs_shift = p->coarse_shift;
   a.nbins = p->nbins;
   return a;
 }

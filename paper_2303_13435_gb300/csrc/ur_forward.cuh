@@ -29,6 +29,8 @@ struct ColArgs {
   // binning
   const int32_t* thr;
   const int16_t* lut;  // k^2 -> bin (-1 outside)
+  const int16_t* crs;  // coarse rank table of k^2 (UR_COARSE_ENTRIES, bin_rank)
+  int crs_shift;
   int nbins;
   float iscale;      // I' = |F~|^2 * iscale (I' = N^3 I)
   double* gsum;      // [nbins] sum of w I'

@@ -265,6 +265,7 @@ static void plan_free(ur_plan* p) {
   if (p->geo) cudaFree(p->geo);
   if (p->d_sched) cudaFree(p->d_sched);
   if (p->binlut) cudaFree(p->binlut);
+  if (p->bincoarse) cudaFree(p->bincoarse);
   free(p->thr_host);
   free(p);
 }
