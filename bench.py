@@ -98,6 +98,23 @@ def profiled_traffic(kernel: str, variant: str):
     return None, None
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Largest value of x over the ranks of the default process group (x itself when
+    there is none): the job time of N replicas is that of the slowest one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every rank processes units_per_rank in at most ms_max."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def workload(n: int):
     from paper_2303_13435_gb300 import inputs
     d = 10.0 * n / 512.0
@@ -274,10 +291,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_total, "cuda")
     ms_step = ms_max / args.steps
 
     # per-kernel averages
@@ -343,13 +357,10 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, "cuda")
 
     out = {
-        "metric": METRIC, "value": world * n ** 3 / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_rate(n ** 3, ms_step, world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"mof512 sphere 10 nm, {n}^3 FP32 grid, {P} nonzero planes, 512 log Q bins, "
@@ -366,7 +377,7 @@ def run_ours(args):
         "kernels": kernels,
         "timing": {"value_from": "CUDA-graph replays of the step", "ms_per_step_eager": ms_eager,
                    "kernel_times_from": "library events around each launch, eager pass of the same steps"},
-        "e2e": {"value": world * n ** 3 / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_rate(n ** 3, e2e_ms, world), "unit": UNIT,
                 "h2d_bytes_per_step": int(cell_host.numel() * 4),
                 "d2h_bytes_per_step": int(bins_host.numel() * 8 + dcell_host.numel() * 4 + dmask_host.numel() * 4)},
         "gpu_launches": sum(c for _, c in per.values()),
