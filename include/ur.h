@@ -267,6 +267,13 @@ ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double*
                       const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,
                       void* stream);
 
+/* Completion status of the work queued so far on `stream`: waits for it
+ * (host blocks) and returns UR_OK, or UR_ERR_CUDA with the CUDA error in
+ * ur_last_error() when a kernel or copy on the device failed.  The library's
+ * kernels contain no device-side waits, so there are no timeout words to
+ * report; UR_ERR_TIMEOUT stays reserved for such waits. */
+ur_status ur_sync_status(void* stream);
+
 /* Per-thread event timing of the last ur_fft_intensity on this thread
  * (milliseconds per internal kernel, in launch order); for measurement only.
  * Enabled by ur_set_timing(1).  Returns the number of entries written. */

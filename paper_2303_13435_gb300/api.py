@@ -71,6 +71,7 @@ SIGNATURES = {
     "ur_batch_backward": (_i32, [_vp, _vp]),
     "ur_plan_set_tiles": (_i32, [_vp, _i32, _i32]),
     "ur_plan_set_chunk_planes": (_i32, [_vp, _i32]),
+    "ur_sync_status": (_i32, [_vp]),
     "ur_plan_chunk_planes": (_i32, [_vp]),
     "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
@@ -268,6 +269,11 @@ def fft_intensity_tiled(plan: Plan, cell: torch.Tensor, shape, origin=(0, 0, 0),
                                                                   C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
                                                                   _ptr(ws), ws.numel(), _stream(stream)))
     return bins
+
+
+def sync_status(stream=None) -> None:
+    """Wait for the work queued on `stream`; raises UrError if it failed on the device."""
+    _check("ur_sync_status", lib().ur_sync_status(_stream(stream)))
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20

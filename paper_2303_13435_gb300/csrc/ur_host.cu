@@ -61,6 +61,15 @@ ur_status ur_fault_point(const char* site) {
   return UR_OK;
 }
 
+extern "C" ur_status ur_sync_status(void* stream) {
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    ur_set_error("ur_sync_status: %s", cudaGetErrorString(e));
+    return UR_ERR_CUDA;
+  }
+  return UR_OK;
+}
+
 extern "C" void ur_fault_reset(void) {
   std::lock_guard<std::mutex> lk(g_fault_mu);
   g_fault_loaded = false;

@@ -159,6 +159,16 @@ def test_F_out_matches_eq1():
     assert err < 2e-6, err
 
 
+def test_sync_status_after_queued_work():
+    w = mof(64, 30)
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    bins = api.fft_intensity(plan, dev(rho[z0:z0 + nz]))
+    api.sync_status()  # raises on a device-side failure
+    assert int(bins[0].sum().item()) > 0
+
+
 def test_fp16_ed_forward():
     w = mof(128, 60)
     rho16 = oracle_density(w, out_dtype="f16")
