@@ -393,3 +393,48 @@ def test_mof512_full_size_forward_and_adjoint(keep_f):
     em = normwise(dmask.cpu().numpy(), gm)
     print("mof512 adjoint", eu, em)
     assert eu <= GRAD_RTOL and em <= GRAD_RTOL
+
+
+@pytest.mark.parametrize("n,keep_f", [(1024, False), (2048, True)])
+def test_large_grid_adjoint_directional_derivative(n, keep_f):
+    """Grids beyond the oracle's reach (1024^3: 512-thread column blocks and block-barrier
+    rows; 2048^3: 1024-thread column blocks): for L = sum_j c_j mean_j, a quadratic in the
+    cell and in the mask weights, the central difference (L(p + d) - L(p - d)) / 2 equals
+    <dL/dp, d> up to rounding.  1024^3 runs with random per-voxel weights (dL/du and dL/dm),
+    2048^3 with the sphere (dL/du, F kept)."""
+    w = mof(n, 0.4 * n, nbins=200)
+    cell = dev(w.cell)
+    half = int(0.2 * n) + 2
+    z0, nz = n // 2 - half, 2 * half
+    g = torch.Generator(device="cpu").manual_seed(n)
+    weights = None
+    shape = w.shape
+    if n <= 1024:
+        wt = torch.zeros((n, n, n), dtype=torch.float32)
+        wt[z0:z0 + nz] = torch.rand((nz, n, n), generator=g)
+        weights = wt.cuda()
+        shape = inputs.Shape(inputs.SHAPE_WEIGHTS)
+    plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    Fh = torch.empty((n, n, n // 2 + 1, 2), device="cuda") if keep_f else None
+    b0 = api.fft_intensity_tiled(plan, cell, shape, weights=weights, ws=ws, F_out=Fh)
+    m0 = b0[4].double()
+    c = torch.where(torch.isfinite(m0) & (m0 > 0), 1.0 / torch.nan_to_num(m0, nan=1.0).clamp(min=1e-300), 0.0)
+    dcell, dmask = api.backward(plan, c, b0, cell, shape, ws, weights=weights, F=Fh, want_mask=weights is not None)
+
+    def loss(cc, wts):
+        b = api.fft_intensity_tiled(plan, cc, shape, weights=wts, ws=ws)
+        return float((c * torch.nan_to_num(b[4].double(), nan=0.0)).sum().item())
+
+    d = (torch.randn(cell.shape, generator=g) * 0.01 * float(cell.abs().mean())).cuda()
+    fd = (loss(cell + d, weights) - loss(cell - d, weights)) / 2.0
+    an = float((dcell.double() * d.double()).sum().item())
+    print(n, "dL/du", fd, an)
+    assert math.isclose(fd, an, rel_tol=2e-3), (fd, an)
+    if weights is not None:
+        e = torch.zeros_like(weights)
+        e[z0:z0 + nz] = (torch.randn((nz, n, n), generator=g) * 0.01).cuda()
+        fdm = (loss(cell, weights + e) - loss(cell, weights - e)) / 2.0
+        anm = float((dmask.double() * e.double()).sum().item())
+        print(n, "dL/dm", fdm, anm)
+        assert math.isclose(fdm, anm, rel_tol=2e-3), (fdm, anm)
