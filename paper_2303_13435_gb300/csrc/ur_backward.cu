@@ -204,6 +204,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
     GradArgs g;
     memset(&g, 0, sizeof g);
     g.tw = p->tw;
+    g.stw = p->stw + p->stw_m_off;
     g.cell = cell;
     g.ucell = ucell;
     if (origin) {

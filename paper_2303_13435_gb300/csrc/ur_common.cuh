@@ -429,6 +429,8 @@ struct ur_plan {
   int ed_dtype, z0, nz, nbins;
   int device, num_sms;
   float2* tw;        // device [n]
+  float2* stw;       // power-of-two path: stage twiddles of the N-point and (at stw_m_off) the N/2-point transforms
+  int stw_m_off;
   int32_t* thr;      // device [nbins+1]
   int16_t* binlut;     // device [3 (N/2)^2 + 1]: bin of k^2 = s, -1 outside every bin
   int16_t* bincoarse;  // device [UR_COARSE_ENTRIES]: bin_rank of s = i << coarse_shift

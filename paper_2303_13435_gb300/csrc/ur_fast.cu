@@ -39,11 +39,16 @@ __device__ __forceinline__ int p2pad(int i) { return i + (i >> 4); }
 
 constexpr int ipow8(int s) { return s == 0 ? 1 : 8 * ipow8(s - 1); }
 
-// Butterflies of one stage.  Thread j runs 8/R butterflies b = j + i L/8; the
-// inputs of butterfly i are v[i + (8/R) r], r < R; k = b mod NS; twiddle
-// exp(-+2 pi i r k/(NS R)) read from a table of exp(-2 pi i t/(L tws)).
-template <int L, int R, int NS, bool INV>
-__device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const float2* __restrict__ tw, int tws) {
+// Offset (float2) of stage S >= 1 in the stage twiddle table of an L-point transform:
+// the stages before S are radix 8, with 8^s rows of 8 slots each.
+constexpr int p2_stage_off(int S) { return S <= 1 ? 0 : p2_stage_off(S - 1) + 8 * ipow8(S - 1); }
+
+// Butterflies of stage S.  Thread j runs 8/R butterflies b = j + i L/8; the
+// inputs of butterfly i are v[i + (8/R) r], r < R; k = b mod NS; the twiddles
+// exp(-+2 pi i r k/(NS R)), r = 1 .. R-1, are row k of the stage's block of the
+// stage table (plan-built in float64, stored float32), read as 16-byte pairs.
+template <int L, int R, int NS, int S, bool INV>
+__device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const float2* __restrict__ stw) {
   constexpr int T = L / 8, NB = 8 / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
@@ -52,9 +57,17 @@ __device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const floa
     float2 a[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) a[r] = v[i + NB * r];
-    if (NS > 1) {
+    if constexpr (NS > 1) {
+      const float4* row = reinterpret_cast<const float4*>(stw + p2_stage_off(S) + k * 8);
+      float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = twmul<INV>(a[r], __ldg(tw + (r * k * (L / (NS * R))) * tws));
+      for (int h = 0; h < R / 2; ++h) {
+        const float4 t = __ldg(row + h);
+        w[2 * h] = make_float2(t.x, t.y);
+        w[2 * h + 1] = make_float2(t.z, t.w);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) a[r] = twmul<INV>(a[r], w[r]);
     }
     dft<R, INV>(a);
 #pragma unroll
@@ -96,26 +109,27 @@ __device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line,
 
 template <int L, bool INV, bool WS, int S>
 struct P2Run {
-  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws,
+  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ stw,
                                              unsigned wmask) {
     constexpr int NST = P2<L>::NST, NFULL = P2<L>::NFULL, REM = P2<L>::REM;
     if constexpr (S < NST) {
       constexpr int R = (S < NFULL) ? 8 : (1 << REM);
       constexpr int NS = ipow8(S);
-      p2_butterflies<L, R, NS, INV>(v, j, tw, tws);
+      p2_butterflies<L, R, NS, S, INV>(v, j, stw);
       if constexpr (S + 1 < NST) p2_exchange<L, R, NS, WS>(v, j, line, wmask);
-      P2Run<L, INV, WS, S + 1>::run(v, j, line, tw, tws, wmask);
+      P2Run<L, INV, WS, S + 1>::run(v, j, line, stw, wmask);
     }
   }
 };
 
 // Whole line transform.  WS = false: every thread of the block must call it
 // (block barriers); WS = true: the L/8 threads of a line share a warp and all
-// of them (the lanes in wmask) must call it.
+// of them (the lanes in wmask) must call it.  stw: the stage twiddle table of
+// the L-point transform.
 template <int L, bool INV, bool WS = false>
-__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ tw, int tws,
+__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ stw,
                                        unsigned wmask = 0xffffffffu) {
-  P2Run<L, INV, WS, 0>::run(v, j, line, tw, tws, wmask);
+  P2Run<L, INV, WS, 0>::run(v, j, line, stw, wmask);
 }
 
 // ---------------------------------------------------------------------------
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
     for (int q = 0; q < 8; ++q) nz |= (v[q].x != 0.f) || (v[q].y != 0.f);
     zero_row = (__ballot_sync(wmask, nz) & wmask) == 0u;
   }
-  if (!zero_row) p2_fft<M, false, WS>(v, j, line, a.tw, 2, wmask);
+  if (!zero_row) p2_fft<M, false, WS>(v, j, line, a.stw, wmask);
   // split step: X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2
   if (!zero_row) {
 #pragma unroll
@@ -312,14 +326,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     atomicMax(&s_bhi, hi_bin);
   }
   if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
-    p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.tw, 1);
+    p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.stw);
     if (valid) {
       const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
 #pragma unroll
       for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
     }
   } else if (MODE == P2_Z_BIN) {
-    p2_fft<N, false>(v, j, line, a.tw, 1);
+    p2_fft<N, false>(v, j, line, a.stw);
     if (a.fout && valid) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) a.fout[(long long)(j + q * T) * N * H + col] = cscale(v[q], a.fscale);
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       }
     }
   } else {  // P2_Z_ADJ
-    if (!a.skip_fwd) p2_fft<N, false>(v, j, line, a.tw, 1);
+    if (!a.skip_fwd) p2_fft<N, false>(v, j, line, a.stw);
     // scale of element kz: sigma of the bin of k^2 = c2 + m^2, m = |signed kz|
     const int nb = a.nbins;
 #pragma unroll
@@ -412,7 +426,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       const int b = bin_rank(crs, a.crs_shift, thr, nb, c2 + m * m);
       v[q] = cscale(v[q], (b >= 0 && b < nb) ? hs[b] : 0.f);
     }
-    p2_fft<N, true>(v, j, line, a.tw, 1);
+    p2_fft<N, true>(v, j, line, a.stw);
     if (valid) {
       const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
 #pragma unroll
@@ -470,7 +484,7 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
     v[q] = make_float2(e.x - o.y, e.y + o.x);
   }
   p2_sync<WS>(wmask);
-  p2_fft<M, true, WS>(v, j, line, a.tw, 2, wmask);
+  p2_fft<M, true, WS>(v, j, line, a.stw, wmask);
   const float* crow = a.cell + ((long long)cz * U + cy) * U;
   RowMask rm;
   rm.init(a.sh, valid ? y : 0, z);

@@ -14,6 +14,7 @@ struct RowArgs {
   ShapeArgs sh;
   const float* weights;    // GEN = 1 with UR_SHAPE_WEIGHTS: full-box weights
   const float2* tw;        // table exp(-2 pi i t / N), t < N
+  const float2* stw;       // stage twiddles of the N/2-point transform (power-of-two kernels)
 };
 
 struct GradArgs {
@@ -22,6 +23,7 @@ struct GradArgs {
   int z0;                  // first absolute plane of this launch
   int rb;                  // rows per block (set by the launcher)
   const float2* tw;
+  const float2* stw;       // stage twiddles of the N/2-point transform
   const float* cell;
   int ucell, ox, oy, oz;
   ShapeArgs sh;

@@ -576,6 +576,7 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.sched = p->d_sched;
   a.nst = p->sched_n.nst;
   a.tw = p->tw;
+  a.stw = p->stw;
   a.thr = p->thr;
   a.lut = p->binlut;
   a.crs = p->bincoarse;
@@ -595,6 +596,7 @@ static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long npl
   for (long long p0 = 0; p0 < nplanes; p0 += step) {
     const long long np = (p0 + step <= nplanes) ? step : nplanes - p0;
     RowArgs r = ra;
+    r.stw = p->stw ? p->stw + p->stw_m_off : nullptr;
     r.X = X + p0 * n * H;
     r.nrows = np * n;
     r.z0 = ra.z0 + (int)p0;

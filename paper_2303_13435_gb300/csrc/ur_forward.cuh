@@ -26,6 +26,7 @@ struct ColArgs {
   const StageInfo* sched;
   int nst;
   const float2* tw;
+  const float2* stw;   // stage twiddles of the N-point transform (power-of-two kernels)
   // binning
   const int32_t* thr;
   const int16_t* lut;  // k^2 -> bin (-1 outside)

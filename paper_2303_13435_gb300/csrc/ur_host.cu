@@ -10,7 +10,7 @@
 #include <mutex>
 #include <string>
 
-#include "ur_forward.cuh"
+#include "ur_fast.cuh"
 
 // ---------------------------------------------------------------------------
 // Errors
@@ -179,6 +179,36 @@ extern "C" int64_t ur_selftest_fastdiv(void) {
   return bad;
 }
 
+// Stage twiddles of the compile-time power-of-two transforms of length L = 2^lg:
+// radix-8 Stockham stages (the last one radix 4 or 2 when lg is not a multiple of 3).
+// Stage S >= 1 has NS = 8^S butterfly classes k and radix R; its rows hold
+// exp(-2 pi i r k / (NS R)) for r < R at row k (8 slots, unused ones 0), so a
+// butterfly reads its R - 1 twiddles with at most four 16-byte loads.  Row blocks
+// follow each other by stage.  Returns the number of float2 written (out may be
+// NULL to count).
+static size_t stage_twiddles(int lg, float2* out) {
+  const int nfull = lg / 3, rem = lg % 3, nst = nfull + (rem ? 1 : 0);
+  size_t off = 0;
+  long long ns = 1;
+  for (int st = 0; st < nst; ++st) {
+    const int R = st < nfull ? 8 : (1 << rem);
+    if (st >= 1) {
+      for (long long k = 0; k < ns; ++k)
+        for (int r = 0; r < 8; ++r) {
+          float2 w = make_float2(0.f, 0.f);
+          if (r < R) {
+            const double a = 2.0 * M_PI * (double)(r * k) / (double)(ns * R);
+            w = make_float2((float)cos(a), (float)(-sin(a)));
+          }
+          if (out) out[off + (size_t)k * 8 + r] = w;
+        }
+      off += (size_t)ns * 8;
+    }
+    ns *= R;
+  }
+  return off;
+}
+
 // Butterfly check on the host: every compile-time radix of the row and column
 // engines against a direct float64 DFT, forward and inverse, on seeded inputs.
 // Returns the largest error relative to the input's L2 norm.
@@ -270,6 +300,7 @@ static bool smooth_2357(int v) {
 static void plan_free(ur_plan* p) {
   if (!p) return;
   if (p->tw) cudaFree(p->tw);
+  if (p->stw) cudaFree(p->stw);
   if (p->thr) cudaFree(p->thr);
   if (p->geo) cudaFree(p->geo);
   if (p->d_sched) cudaFree(p->d_sched);
@@ -352,6 +383,26 @@ extern "C" ur_status ur_plan_create(const ur_grid_desc* g, const double* edges, 
     plan_free(p);
     ur_set_error("ur_plan_create: device allocation of plan tables failed");
     return UR_ERR_OOM;
+  }
+  if (ur_fast_supported(n)) {
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const size_t cn = stage_twiddles(lg, nullptr), cm = stage_twiddles(lg - 1, nullptr);
+    float2* st_h = (float2*)malloc(sizeof(float2) * (cn + cm + 1));
+    stage_twiddles(lg, st_h);
+    stage_twiddles(lg - 1, st_h + cn);
+    p->stw_m_off = (int)cn;
+    const cudaError_t ea = cudaMalloc(&p->stw, sizeof(float2) * (cn + cm + 1));
+    const cudaError_t eb = ea == cudaSuccess ? cudaMemcpy(p->stw, st_h, sizeof(float2) * (cn + cm + 1),
+                                                          cudaMemcpyHostToDevice) : ea;
+    free(st_h);
+    if (eb != cudaSuccess) {
+      free(tw_h);
+      free(thr32);
+      plan_free(p);
+      ur_set_error("ur_plan_create: stage twiddle table: %s", cudaGetErrorString(eb));
+      return ea != cudaSuccess ? UR_ERR_OOM : UR_ERR_CUDA;
+    }
   }
   cudaError_t e4 = cudaMemcpy(p->tw, tw_h, sizeof(float2) * n, cudaMemcpyHostToDevice);
   cudaError_t e5 = cudaMemcpy(p->thr, thr32, sizeof(int32_t) * (nbins + 1), cudaMemcpyHostToDevice);
