@@ -206,6 +206,35 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
   }
   if (!zero_row) p2_fft<M, false, WS>(v, j, line, a.stw, wmask);
   // split step: X[k] = (Z[k] + conj Z[M-k])/2 - i W_N^k (Z[k] - conj Z[M-k])/2
+  if constexpr (WS) {
+    // Z[M - k], k = j + qT, is register 7 - q of lane T - j of the same row (j >= 1);
+    // lane j = 0 holds its own partners: Z[M - qT] = its register 8 - q, and Z[0]
+    const int src = ((threadIdx.x & 31) & ~(T - 1)) | ((T - j) & (T - 1));
+    float2* X = a.X + (valid ? r : 0) * H;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float2 zm = make_float2(__shfl_sync(wmask, v[7 - q].x, src), __shfl_sync(wmask, v[7 - q].y, src));
+      if (j == 0) zm = v[(8 - q) & 7];
+      if (!valid) continue;
+      const int k = j + q * T;
+      if (zero_row) {
+        X[k] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const float2 zk = v[q], zc = cconj(zm);
+      const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+      const float2 d = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
+      const float2 o = make_float2(d.y, -d.x);
+      X[k] = cadd(e, cmul(__ldg(a.tw + k), o));
+    }
+    if (valid && j == 0) {  // k = M: Z[M] = Z[0]
+      const float2 zk = v[0], zc = cconj(v[0]);
+      const float2 d = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
+      X[M] = cadd(make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)),
+                  cmul(__ldg(a.tw + M), make_float2(d.y, -d.x)));
+    }
+    return;
+  }
   if (!zero_row) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
@@ -461,29 +490,46 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
   for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
   float2* line = sm + t * PITCH;
   const float2* Yrow = a.Y + ((long long)(z - a.ybase_z) * N + (valid ? y : 0)) * H;
-  {
-    // all nine loads of the row (k = j + q T, and k = M) are issued before any is stored
-    float2 ld[9];
+  // all nine loads of the row (k = j + q T, and k = M) are issued together
+  float2 ld[9];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) ld[q] = valid ? __ldg(Yrow + j + q * T) : make_float2(0.f, 0.f);
-    ld[8] = (valid && j == 0) ? __ldg(Yrow + M) : make_float2(0.f, 0.f);
+  for (int q = 0; q < 8; ++q) ld[q] = valid ? __ldg(Yrow + j + q * T) : make_float2(0.f, 0.f);
+  ld[8] = (valid && j == 0) ? __ldg(Yrow + M) : make_float2(0.f, 0.f);
+  float2 v[8];
+  if constexpr (WS) {
+    // X[M - k], k = j + qT, is load 7 - q of lane T - j of the same row (j >= 1); lane
+    // j = 0 holds its own partners: X[M - qT] = its load 8 - q (X[M] for q = 0)
+    const int src = ((threadIdx.x & 31) & ~(T - 1)) | ((T - j) & (T - 1));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = j + q * T;
+      float2 xb = make_float2(__shfl_sync(wmask, ld[7 - q].x, src), __shfl_sync(wmask, ld[7 - q].y, src));
+      if (j == 0) xb = ld[8 - q];
+      const float2 xa = ld[q];
+      const float2 w = __ldg(a.tw + k);
+      const float2 e = cadd(xa, cconj(xb));
+      const float2 d = csub(xa, cconj(xb));
+      const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);
+      v[q] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    __syncthreads();  // orders the zeroing of acc before any accumulation
+  } else {
 #pragma unroll
     for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = ld[q];
     if (j == 0) line[p2pad(M)] = ld[8];
-  }
-  __syncthreads();  // also orders the zeroing of acc before any accumulation
-  float2 v[8];
+    __syncthreads();  // also orders the zeroing of acc before any accumulation
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int k = j + q * T;
-    const float2 xa = line[p2pad(k)], xb = line[p2pad(M - k)];
-    const float2 w = __ldg(a.tw + k);
-    const float2 e = cadd(xa, cconj(xb));
-    const float2 d = csub(xa, cconj(xb));
-    const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);
-    v[q] = make_float2(e.x - o.y, e.y + o.x);
+    for (int q = 0; q < 8; ++q) {
+      const int k = j + q * T;
+      const float2 xa = line[p2pad(k)], xb = line[p2pad(M - k)];
+      const float2 w = __ldg(a.tw + k);
+      const float2 e = cadd(xa, cconj(xb));
+      const float2 d = csub(xa, cconj(xb));
+      const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);
+      v[q] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    __syncthreads();  // the transform's first exchange reuses the lines
   }
-  p2_sync<WS>(wmask);
   p2_fft<M, true, WS>(v, j, line, a.stw, wmask);
   const float* crow = a.cell + ((long long)cz * U + cy) * U;
   RowMask rm;
