@@ -224,9 +224,6 @@ def run_ours(args):
     bins = api.new_bins(plan)
     dcell = torch.empty_like(cell)
     dmask = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
-    # the forward keeps the half spectrum F (539 MB at 512^3) for the adjoint, which then
-    # scales and inverts it instead of recomputing it along z from the plane-pass output
-    Fh = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     # target curve: closed-form sphere of the particle's electron count (loss input)
@@ -239,12 +236,12 @@ def run_ours(args):
     target = torch.from_numpy(inputs.sphere_target_curve(qm, radius, ne) / float(n) ** 6 + 1e-300).cuda()
 
     def step():
-        api.fft_intensity_tiled(plan, cell, w.shape, bins=bins, F_out=Fh, ws=ws)
+        api.fft_intensity_tiled(plan, cell, w.shape, bins=bins, ws=ws)
         mean = bins[api.BIN_MEAN]
         ok = torch.isfinite(mean) & (mean > 0)
         d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)
         g = torch.where(ok, 2.0 * d / (torch.where(ok, mean, 1.0) * ok.sum().clamp(min=1)), 0.0)
-        api.backward(plan, g, bins, cell, w.shape, ws, F=Fh, dl_dcell=dcell, dl_dmask=dmask)
+        api.backward(plan, g, bins, cell, w.shape, ws, dl_dcell=dcell, dl_dmask=dmask)
 
     for _ in range(args.warmup):
         step()
@@ -302,7 +299,7 @@ def run_ours(args):
         s[1] += 1
     # kernel_bytes() is per step; a kernel launched in plane chunks moves that over
     # launches/steps launches, so bytes per launch = per-step bytes * steps / launches.
-    kb = kernel_bytes(n, P, w.ucell, store_f=True)
+    kb = kernel_bytes(n, P, w.ucell)
     dom = max(per.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_cnt) = dom
     hbm, src = peaks()
@@ -343,7 +340,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     fonly_ms = max_over_ranks(e0.elapsed_time(e1), "cuda") / args.steps
     fonly_frac = fwd_gate_bytes / (fonly_ms * 1e-3) / 1e9 / hbm
-    traffic, traffic_src = profiled_traffic(KERNEL_OF.get(dom_name, ""), "keepF")
+    traffic, traffic_src = profiled_traffic(KERNEL_OF.get(dom_name, ""), "recompute")
 
     # end to end through the public API with host buffers
     cell_host = torch.from_numpy(w.cell).pin_memory()
@@ -354,12 +351,12 @@ def run_ours(args):
 
     def e2e_step():
         cell_dev.copy_(cell_host, non_blocking=True)
-        api.fft_intensity_tiled(plan, cell_dev, w.shape, bins=bins, F_out=Fh, ws=ws)
+        api.fft_intensity_tiled(plan, cell_dev, w.shape, bins=bins, ws=ws)
         mean = bins[api.BIN_MEAN]
         ok = torch.isfinite(mean) & (mean > 0)
         d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)
         g = torch.where(ok, 2.0 * d / (torch.where(ok, mean, 1.0) * ok.sum().clamp(min=1)), 0.0)
-        api.backward(plan, g, bins, cell_dev, w.shape, ws, F=Fh, dl_dcell=dcell, dl_dmask=dmask)
+        api.backward(plan, g, bins, cell_dev, w.shape, ws, dl_dcell=dcell, dl_dmask=dmask)
         bins_host.copy_(bins, non_blocking=True)
         dcell_host.copy_(dcell, non_blocking=True)
         dmask_host.copy_(dmask, non_blocking=True)
@@ -381,7 +378,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"mof512 sphere 10 nm, {n}^3 FP32 grid, {P} nonzero planes, 512 log Q bins, "
-                               "forward + adjoint (dL/d cell, dL/d mask); F kept for the adjoint",
+                               "forward + adjoint (dL/d cell, dL/d mask) recomputing F along z",
                    "grid": n, "nonzero_planes": P, "bins": 512, "cell": f"{w.ucell}^3, 2.6 nm, 60 atoms, seed 0",
                    "l2": "inputs larger than L2 (ED slab, intermediates); no flush",
                    "parallelism": f"replicas x{world}"},

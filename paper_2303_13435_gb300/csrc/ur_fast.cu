@@ -306,6 +306,29 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     ky = o < M ? o : o - N;
   }
   const int c2 = kx * kx + ky * ky;
+  // z passes: columns whose k^2 = kx^2 + ky^2 already lies at or beyond the closing
+  // threshold reach no bin at any kz.  A block made only of such columns has nothing to
+  // bin (forward, when F is not written) or only zero scales (adjoint: its output is
+  // zero), so it skips the loads and the transforms.
+  if ((MODE == P2_Z_BIN && binning && !a.fout) || (MODE == P2_Z_ADJ && binning)) {
+    const int tn = __ldg(a.thr + a.nbins);
+    bool beyond = true;
+#pragma unroll
+    for (int t = 0; t < TX; ++t) {
+      const int cc = col0 + t;
+      if (cc >= a.ncols) break;
+      const int oo = cc / H, kxx = cc - oo * H, kyy = oo < M ? oo : oo - N;
+      beyond = beyond && (kxx * kxx + kyy * kyy >= tn);
+    }
+    if (beyond) {  // uniform over the block
+      if (MODE == P2_Z_ADJ && valid) {
+        const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = make_float2(0.f, 0.f);
+      }
+      return;
+    }
+  }
   // z passes: the bin thresholds go to shared memory.  The adjoint, which needs the bin
   // of every element, also stages the coarse rank table and its per-bin scales there (no
   // gathers from global memory per element).  The forward binning needs only a few bins
