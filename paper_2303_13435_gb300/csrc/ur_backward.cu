@@ -186,6 +186,10 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
     a.skip_fwd = 0;
   }
   const long long tiles = (a.ncols + a.TX - 1) / a.TX;
+  // power-of-two path: columns with kx^2 + ky^2 at or beyond the closing threshold get zero
+  // scales at every kz; the z pass leaves them unwritten and the y pass reads them as zeros
+  const int k2_zero = p->fast ? (int)(p->thr_host[nb] < 0x7fffffff ? p->thr_host[nb] : 0x7fffffff) : 0x7fffffff;
+  if (p->fast) a.k2_zero = k2_zero;
   ur_timing_begin("adj_cols_z", s);
   if (p->fast) {
     UR_TRY(ur_fast_cols(n, 3 /* z adjoint */, a, s));
@@ -231,6 +235,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
       b.nload = n;
       b.zoff = 0;
       b.nbins = 0;
+      b.k2_zero = k2_zero;
       ur_timing_begin("adj_cols_y", s);
       UR_TRY(ur_fast_cols(n, 1 /* y inverse */, b, s));
       ur_timing_end(s);

@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       beyond = beyond && (kxx * kxx + kyy * kyy >= tn);
     }
     if (beyond) {  // uniform over the block
-      if (MODE == P2_Z_ADJ && valid) {
+      // adjoint: the output columns are zero; unless the caller reads them as zeros
+      // without loading (k2_zero), write them
+      if (MODE == P2_Z_ADJ && valid && a.k2_zero == 0x7fffffff) {
         const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
 #pragma unroll
         for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = make_float2(0.f, 0.f);
@@ -357,7 +359,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
   float2 v[8];
-  if (a.zoff == 0 && a.nload == N) {  // whole column present (y passes, F given)
+  if (MODE == P2_Y_INV && a.k2_zero != 0x7fffffff) {
+    // adjoint y pass: elements with kx^2 + ky^2 >= k2_zero are zero (the z pass left them
+    // unwritten) and are not read
+    const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);
+    const long long step = (long long)T * a.S;
+    const int kx2 = kx * kx;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int li = j + q * T, kyy = li < M ? li : li - N;
+      v[q] = (valid && kx2 + kyy * kyy < a.k2_zero) ? __ldg(src + q * step) : make_float2(0.f, 0.f);
+    }
+  } else if (a.zoff == 0 && a.nload == N) {  // whole column present (y passes, F given)
     const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);
     const long long step = (long long)T * a.S;
 #pragma unroll

@@ -579,6 +579,7 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.stw = p->stw;
   a.thr = p->thr;
   a.lut = p->binlut;
+  a.k2_zero = 0x7fffffff;
   a.crs = p->bincoarse;
   a.crs_shift = p->coarse_shift;
   a.nbins = p->nbins;

@@ -41,6 +41,9 @@ struct ColArgs {
   // adjoint
   const float* sigma;  // per-bin scale of F~ along z (adjoint)
   int skip_fwd;        // 1: the loaded column is already the spectrum along z
+  int k2_zero;         // power-of-two adjoint: spectrum columns with kx^2 + ky^2 >= k2_zero are
+                       // zero; the z pass may leave them unwritten and the y pass does not read
+                       // them (0x7fffffff: none)
 };
 
 // generic adjoint row pass (one block: a batch of rows wrapping onto one cell row)
