@@ -72,6 +72,13 @@ struct RowMask {
   }
 };
 
+// Sphere row (y, z) outside the particle: the test of RowMask::empty with the same
+// roundings, for kernels that hold no RowMask.
+__device__ __forceinline__ bool sphere_row_empty(const ShapeArgs& sh, int y, int z) {
+  const float dy = __fsub_rn((float)y, sh.cy), dz = __fsub_rn((float)z, sh.cz);
+  return __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)) > __fmul_rn(sh.s, sh.s);
+}
+
 static inline ShapeArgs ur_shape_args(const ur_shape* shape) {
   ShapeArgs sh;
   sh.kind = shape->kind;

@@ -167,6 +167,11 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
     rm.init(a.sh, y, z);
     const int U = a.ucell;
     const float* wrow = a.weights ? a.weights + ((long long)z * N + y) * N : nullptr;
+    if constexpr (WS) {
+      // rows outside the sphere: not written at all when the y pass knows to skip them
+      // (the condition is uniform over the row's lanes, which only sync among themselves)
+      if (a.skip_empty && valid && !wrow && rm.empty()) return;
+    }
     // rows the mask excludes entirely are zero (cell values are finite)
     if (valid && (wrow || !rm.empty())) {
       const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
@@ -359,7 +364,18 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
   float2 v[8];
-  if (MODE == P2_Y_INV && a.k2_zero != 0x7fffffff) {
+  if (MODE == P2_Y_FWD && a.row_skip) {
+    // forward y pass over a generated sphere: rows y outside the particle in plane z are
+    // zero and were not written by the row pass
+    const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);
+    const long long step = (long long)T * a.S;
+    const int z = a.gen_z0 + col / H;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int y = j + q * T;
+      v[q] = (valid && !sphere_row_empty(a.sh, y, z)) ? __ldg(src + q * step) : make_float2(0.f, 0.f);
+    }
+  } else if (MODE == P2_Y_INV && a.k2_zero != 0x7fffffff) {
     // adjoint y pass: elements with kx^2 + ky^2 >= k2_zero are zero (the z pass left them
     // unwritten) and are not read
     const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);

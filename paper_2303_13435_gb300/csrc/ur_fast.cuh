@@ -15,6 +15,7 @@ struct RowArgs {
   const float* weights;    // GEN = 1 with UR_SHAPE_WEIGHTS: full-box weights
   const float2* tw;        // table exp(-2 pi i t / N), t < N
   const float2* stw;       // stage twiddles of the N/2-point transform (power-of-two kernels)
+  int skip_empty;          // GEN = 1, sphere, N <= 512: rows outside the particle are not written
 };
 
 struct GradArgs {

@@ -602,6 +602,10 @@ static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long npl
     r.nrows = np * n;
     r.z0 = ra.z0 + (int)p0;
     if (!gen) r.ed = (const char*)ra.ed + p0 * (long long)n * n * (p->ed_dtype == UR_F16 ? 2 : 4);
+    // generated sphere on rows of at most one warp: the row pass leaves the rows outside the
+    // particle unwritten and the y pass reads them as zeros
+    const bool skip = gen && p->fast && n <= 512 && ra.sh.kind == UR_SHAPE_SPHERE && !ra.weights;
+    r.skip_empty = skip ? 1 : 0;
     ur_timing_begin("rows_r2c", s);
     if (p->fast) {
       UR_TRY(ur_fast_rows(n, r, gen, p->ed_dtype == UR_F16, s));
@@ -626,6 +630,11 @@ static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long npl
     a.nload = n;
     a.zoff = 0;
     a.nbins = 0;
+    if (skip) {
+      a.row_skip = 1;
+      a.gen_z0 = r.z0;
+      a.sh = ra.sh;
+    }
     ur_timing_begin("cols_y", s);
     if (p->fast) {
       UR_TRY(ur_fast_cols(n, 0 /* y forward */, a, s));

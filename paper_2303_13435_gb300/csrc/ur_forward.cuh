@@ -41,6 +41,9 @@ struct ColArgs {
   // adjoint
   const float* sigma;  // per-bin scale of F~ along z (adjoint)
   int skip_fwd;        // 1: the loaded column is already the spectrum along z
+  int row_skip;        // power-of-two forward y pass over a generated sphere density: rows
+  int gen_z0;          // (y, gen_z0 + plane) outside the sphere are zero and were not
+  ShapeArgs sh;        // written by the row pass; they are not read
   int k2_zero;         // power-of-two adjoint: spectrum columns with kx^2 + ky^2 >= k2_zero are
                        // zero; the z pass may leave them unwritten and the y pass does not read
                        // them (0x7fffffff: none)
