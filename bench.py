@@ -5,7 +5,8 @@ Gaussian atoms, 64^3 samples, seed 0) tiled and cut by a 10 nm sphere, 512
 log-spaced Q bins from dq to pi/dx:
   ur_fft_intensity_tiled (the density of the 247 nonzero planes generated
   inside the plane pass, column pass with fused |F|^2 and binning) ->
-  dL/d(mean I) of a log-MSE loss against the closed-form sphere curve ->
+  dL/d(mean I) of a log-MSE loss against the closed-form sphere curve
+  (ur_log_mse_grad) ->
   ur_backward (dL/d cell, dL/d mask).
 All inputs are synthetic and larger than L2 (ED slab 259 MB, intermediate
 520 MB), so no explicit L2 flush is done between steps.
@@ -185,6 +186,7 @@ def kernel_bytes(n: int, P: int, U: int, store_f: bool = False):
         "cols_z_bin": X + (Y if store_f else 0),
         "finalize": 0,
         "sigma": 0,
+        "loss_grad": 0,
         "adj_cols_z": (Y if store_f else X) + Y,
         "adj_cols_y": 2 * Y,
         "adj_rows_grad": Y + 4 * n ** 3 + 4 * U ** 3,
@@ -235,12 +237,11 @@ def run_ours(args):
     radius = 0.5 * 10.0 * n / 512.0
     target = torch.from_numpy(inputs.sphere_target_curve(qm, radius, ne) / float(n) ** 6 + 1e-300).cuda()
 
+    g = torch.empty(plan.nbins, dtype=torch.float64, device="cuda")
+
     def step():
         api.fft_intensity_tiled(plan, cell, w.shape, bins=bins, ws=ws)
-        mean = bins[api.BIN_MEAN]
-        ok = torch.isfinite(mean) & (mean > 0)
-        d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)
-        g = torch.where(ok, 2.0 * d / (torch.where(ok, mean, 1.0) * ok.sum().clamp(min=1)), 0.0)
+        api.log_mse_grad(bins, target, g)
         api.backward(plan, g, bins, cell, w.shape, ws, dl_dcell=dcell, dl_dmask=dmask)
 
     for _ in range(args.warmup):
@@ -352,10 +353,7 @@ def run_ours(args):
     def e2e_step():
         cell_dev.copy_(cell_host, non_blocking=True)
         api.fft_intensity_tiled(plan, cell_dev, w.shape, bins=bins, ws=ws)
-        mean = bins[api.BIN_MEAN]
-        ok = torch.isfinite(mean) & (mean > 0)
-        d = torch.where(ok, torch.log(torch.where(ok, mean, 1.0)) - torch.log(target), 0.0)
-        g = torch.where(ok, 2.0 * d / (torch.where(ok, mean, 1.0) * ok.sum().clamp(min=1)), 0.0)
+        api.log_mse_grad(bins, target, g)
         api.backward(plan, g, bins, cell_dev, w.shape, ws, dl_dcell=dcell, dl_dmask=dmask)
         bins_host.copy_(bins, non_blocking=True)
         dcell_host.copy_(dcell, non_blocking=True)
@@ -485,11 +483,6 @@ def run_batch(args):
     chosen = autotune.tune(plans, cell, shapes, reps=2)
     tune_s = time.time() - t0
 
-    def loss_grad(mean, target, out):
-        ok = torch.isfinite(mean) & (mean > 0)
-        m = torch.where(ok, mean, 1.0)
-        d = torch.where(ok, torch.log(m) - torch.log(target), 0.0)
-        out.copy_(torch.where(ok, 2.0 * d / (m * ok.sum().clamp(min=1)), 0.0))
 
     # looped single-instance path (fast kernels for power-of-two edges)
     ws = [p.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD) for p in plans]
@@ -500,7 +493,7 @@ def run_batch(args):
     def loop_step():
         for i, (p, pl) in enumerate(zip(parts, plans)):
             api.fft_intensity_tiled(pl, cell, p.shape, bins=bins[i], ws=ws[i])
-            loss_grad(bins[i][api.BIN_MEAN], targets[i], gs[i])
+            api.log_mse_grad(bins[i], targets[i], gs[i])
             api.backward(pl, gs[i], bins[i], cell, p.shape, ws[i], dl_dcell=dcell[i], want_mask=False)
 
     batch = api.Batch(plans, cell, shapes)
@@ -508,7 +501,7 @@ def run_batch(args):
     def batch_step():
         batch.forward()
         for i in range(len(plans)):
-            loss_grad(batch.bins[i][api.BIN_MEAN], targets[i], batch.dl_dmean[i])
+            api.log_mse_grad(batch.bins[i], targets[i], batch.dl_dmean[i])
         batch.backward()
 
     def timed(fn, steps):

@@ -267,6 +267,19 @@ ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double*
                       const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,
                       void* stream);
 
+/* Log-I(Q) mean-squared error against a target curve and its gradient, the
+ * loss of the batched workload and of the benchmark step (not in the paper;
+ * the fit of a simulated curve to a measured one that Sec. 3 motivates):
+ *   L = (1/V) sum over valid bins of (ln mean_j - ln target_j)^2, valid = finite
+ *   and positive mean, V = max(number of valid bins, 1);
+ *   dl_dmean_j = 2 (ln mean_j - ln target_j) / (mean_j V) on valid bins, else 0.
+ * bins: device double[UR_BIN_FIELDS][nbins] from a forward; target: device
+ * double[nbins] (positive where bins are valid); loss: device double[1] or NULL;
+ * dl_dmean: device double[nbins] (overwritten), ready for ur_backward.  One
+ * kernel launch, float64 throughout; nbins <= 8192 (UR_ERR_INVALID above). */
+ur_status ur_log_mse_grad(int32_t nbins, const double* bins, const double* target, double* loss, double* dl_dmean,
+                          void* stream);
+
 /* Completion status of the work queued so far on `stream`: waits for it
  * (host blocks) and returns UR_OK, or UR_ERR_CUDA with the CUDA error in
  * ur_last_error() when a kernel or copy on the device failed.  The library's

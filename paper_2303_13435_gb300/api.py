@@ -72,6 +72,7 @@ SIGNATURES = {
     "ur_plan_set_tiles": (_i32, [_vp, _i32, _i32]),
     "ur_plan_set_chunk_planes": (_i32, [_vp, _i32]),
     "ur_sync_status": (_i32, [_vp]),
+    "ur_log_mse_grad": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "ur_plan_chunk_planes": (_i32, [_vp]),
     "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
@@ -269,6 +270,18 @@ def fft_intensity_tiled(plan: Plan, cell: torch.Tensor, shape, origin=(0, 0, 0),
                                                                   C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
                                                                   _ptr(ws), ws.numel(), _stream(stream)))
     return bins
+
+
+def log_mse_grad(bins: torch.Tensor, target: torch.Tensor, dl_dmean: torch.Tensor | None = None,
+                 loss: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dL/d(mean) of the log-I(Q) MSE against `target` (and L into `loss`, a device double[1])."""
+    nb = bins.shape[1]
+    assert bins.dtype == torch.float64 and target.dtype == torch.float64 and target.numel() == nb
+    if dl_dmean is None:
+        dl_dmean = torch.empty(nb, dtype=torch.float64, device=bins.device)
+    _check("ur_log_mse_grad", lib().ur_log_mse_grad(nb, _ptr(bins), _ptr(target), _ptr(loss), _ptr(dl_dmean),
+                                                    _stream(stream)))
+    return dl_dmean
 
 
 def sync_status(stream=None) -> None:

@@ -141,6 +141,70 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
 
 __global__ void __launch_bounds__(256, 2) k_rows_grad(GenGradArgs g) { rows_grad_body(g, blockIdx.x, blockIdx.y); }
 
+// Log-I(Q) MSE and its gradient in one block of 1024 threads: each thread keeps
+// the log differences of its (at most 8) bins in registers, the number of valid
+// bins and the sum of squares are block-reduced, then every bin's gradient is
+// written.  float64 throughout.
+#define UR_LOSS_THREADS 1024
+#define UR_LOSS_PER_THREAD 8
+__global__ void __launch_bounds__(UR_LOSS_THREADS) k_log_mse_grad(int nb, const double* __restrict__ bins,
+                                                                  const double* __restrict__ target,
+                                                                  double* __restrict__ loss, double* __restrict__ g) {
+  __shared__ double s_sum[UR_LOSS_THREADS / 32];
+  __shared__ int s_cnt[UR_LOSS_THREADS / 32];
+  const double* mean = bins + (size_t)UR_BIN_MEAN * nb;
+  double d[UR_LOSS_PER_THREAD], m[UR_LOSS_PER_THREAD];
+  double ss = 0.0;
+  int cnt = 0;
+#pragma unroll
+  for (int u = 0; u < UR_LOSS_PER_THREAD; ++u) {
+    const int j = threadIdx.x + u * UR_LOSS_THREADS;
+    m[u] = j < nb ? mean[j] : 0.0;
+    d[u] = 0.0;
+    if (j < nb && isfinite(m[u]) && m[u] > 0.0) {
+      d[u] = log(m[u]) - log(target[j]);
+      ss += d[u] * d[u];
+      ++cnt;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_down_sync(0xffffffffu, ss, o);
+    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[threadIdx.x >> 5] = ss;
+    s_cnt[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  int ntot = 0;
+  for (int w = 0; w < UR_LOSS_THREADS / 32; ++w) {  // the same order on every thread
+    tot += s_sum[w];
+    ntot += s_cnt[w];
+  }
+  const double nv = (double)(ntot > 0 ? ntot : 1);
+  if (threadIdx.x == 0 && loss) *loss = tot / nv;
+#pragma unroll
+  for (int u = 0; u < UR_LOSS_PER_THREAD; ++u) {
+    const int j = threadIdx.x + u * UR_LOSS_THREADS;
+    if (j < nb) g[j] = (isfinite(m[u]) && m[u] > 0.0) ? 2.0 * d[u] / (m[u] * nv) : 0.0;
+  }
+}
+
+extern "C" ur_status ur_log_mse_grad(int32_t nbins, const double* bins, const double* target, double* loss,
+                                     double* dl_dmean, void* stream) {
+  UR_REQUIRE(nbins >= 1 && bins && target && dl_dmean, "ur_log_mse_grad: bad argument");
+  UR_REQUIRE(nbins <= UR_LOSS_THREADS * UR_LOSS_PER_THREAD, "ur_log_mse_grad: %d bins (at most %d)", nbins,
+             UR_LOSS_THREADS * UR_LOSS_PER_THREAD);
+  cudaStream_t s = (cudaStream_t)stream;
+  ur_timing_begin("loss_grad", s);
+  k_log_mse_grad<<<1, UR_LOSS_THREADS, 0, s>>>(nbins, bins, target, loss, dl_dmean);
+  UR_LAUNCH_CHECK("k_log_mse_grad");
+  ur_timing_end(s);
+  return UR_OK;
+}
+
 extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const double* fwd_bins, const void* F,
                                  const float* cell, int32_t ucell, const int32_t* origin, const ur_shape* shape,
                                  const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,

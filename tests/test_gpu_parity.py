@@ -159,6 +159,22 @@ def test_F_out_matches_eq1():
     assert err < 2e-6, err
 
 
+def test_log_mse_grad_matches_oracle():
+    rng = np.random.default_rng(11)
+    nb = 700
+    bins = np.zeros((api.BIN_FIELDS, nb))
+    bins[4] = rng.uniform(1e-8, 1e-2, nb)
+    bins[4][[5, 99, 300]] = np.nan
+    bins[4][[7, 400]] = 0.0
+    bins[4][450] = -1.0
+    target = rng.uniform(1e-8, 1e-2, nb)
+    L, g = adjoint.loss_log_mse(bins[4], target)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    got = api.log_mse_grad(dev(bins), dev(target), loss=loss).cpu().numpy()
+    assert np.allclose(got, g, rtol=1e-12, atol=0)
+    assert math.isclose(float(loss.item()), L, rel_tol=1e-12)
+
+
 def test_sync_status_after_queued_work():
     w = mof(64, 30)
     rho = oracle_density(w)

@@ -392,3 +392,25 @@ def test_merge_levels_share_forward_scattering():
         ed = density.zoom_out(ed1, f, nout, out_dtype="f32")
         F = scatter.dft3(ed)
         assert math.isclose(scatter.intensity(F)[0, 0, 0] * nout ** 6, ne ** 2, rel_tol=1e-6)
+
+
+def test_log_mse_loss_gradient_matches_central_differences():
+    """The log-I(Q) MSE of the oracle against central differences of its own value;
+    bins that are empty (NaN) or non-positive take no part."""
+    rng = np.random.default_rng(5)
+    mean = rng.uniform(0.5, 2.0, 40)
+    mean[[3, 17]] = np.nan
+    mean[25] = 0.0
+    target = rng.uniform(0.5, 2.0, 40)
+    L, g = adjoint.loss_log_mse(mean, target)
+    ok = np.isfinite(mean) & (mean > 0)
+    assert np.all(g[~ok] == 0.0)
+    h = 1e-6
+    for j in np.flatnonzero(ok)[:10]:
+        mp, mm = mean.copy(), mean.copy()
+        mp[j] += h
+        mm[j] -= h
+        fd = (adjoint.loss_log_mse(mp, target)[0] - adjoint.loss_log_mse(mm, target)[0]) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(g[j]))
+    # value: a plain mean of squared log ratios over the valid bins
+    assert math.isclose(L, float(np.mean(np.log(mean[ok] / target[ok]) ** 2)), rel_tol=1e-12)
