@@ -1,4 +1,4 @@
-// Power-of-two grid edges (64 <= N <= 1024): compile-time transforms.
+// Power-of-two grid edges (64 <= N <= 4096): compile-time transforms.
 //
 // A length-L line is held by L/8 threads, eight complex values each
 // (thread j holds positions j + q L/8, q = 0..7).  Each Stockham stage is a
