@@ -316,15 +316,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   // bin (forward, when F is not written) or only zero scales (adjoint: its output is
   // zero), so it skips the loads and the transforms.
   if ((MODE == P2_Z_BIN && binning && !a.fout) || (MODE == P2_Z_ADJ && binning)) {
-    const int tn = __ldg(a.thr + a.nbins);
-    bool beyond = true;
-#pragma unroll
-    for (int t = 0; t < TX; ++t) {
-      const int cc = col0 + t;
-      if (cc >= a.ncols) break;
-      const int oo = cc / H, kxx = cc - oo * H, kyy = oo < M ? oo : oo - N;
-      beyond = beyond && (kxx * kxx + kyy * kyy >= tn);
-    }
+    // every thread votes for its own column (columns past the end count as beyond)
+    const bool beyond = __syncthreads_and(!valid || c2 >= __ldg(a.thr + a.nbins));
     if (beyond) {  // uniform over the block
       // adjoint: the output columns are zero; unless the caller reads them as zeros
       // without loading (k2_zero), write them
