@@ -211,6 +211,7 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
                                  void* stream) {
   UR_REQUIRE(p && dl_dmean && fwd_bins && cell && shape && dl_dcell && ws, "ur_backward: null argument");
   UR_REQUIRE(ucell >= 1, "ur_backward: empty cell");
+  UR_REQUIRE(!origin || (origin[0] >= 0 && origin[1] >= 0 && origin[2] >= 0), "ur_backward: origin must be >= 0");
   UR_REQUIRE(ws_bytes >= ur_workspace_size(p, UR_WS_FORWARD | UR_WS_BACKWARD), "ur_backward: workspace %zu < %zu bytes",
              ws_bytes, ur_workspace_size(p, UR_WS_FORWARD | UR_WS_BACKWARD));
   UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_backward: bad shape kind");

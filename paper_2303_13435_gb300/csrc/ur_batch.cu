@@ -94,6 +94,8 @@ extern "C" ur_status ur_batch_create(int32_t count, const ur_batch_item* items, 
     UR_REQUIRE(it.ucell >= 1 && (long long)it.ucell * it.ucell <= 65535, "ur_batch_create: item %d cell edge", i);
     UR_REQUIRE(it.shape.kind >= UR_SHAPE_SPHERE && it.shape.kind <= UR_SHAPE_WEIGHTS, "ur_batch_create: item %d shape", i);
     UR_REQUIRE(it.shape.kind != UR_SHAPE_WEIGHTS || it.weights, "ur_batch_create: item %d needs weights", i);
+    UR_REQUIRE(it.origin[0] >= 0 && it.origin[1] >= 0 && it.origin[2] >= 0, "ur_batch_create: item %d origin must be >= 0",
+               i);
     UR_REQUIRE(((uintptr_t)it.ws % 256) == 0, "ur_batch_create: item %d workspace misaligned", i);
     const bool bwd = it.dl_dmean && it.dl_dcell;
     has_bwd &= bwd ? 1 : 0;

@@ -147,7 +147,7 @@ __device__ __forceinline__ float2 ld_pair<__half>(const __half* p) {
 }
 
 template <int N, int GEN, typename TED>
-__global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
+__global__ void __launch_bounds__(512, 3) k_p2_rows(RowArgs a) {
   constexpr int M = N / 2, H = M + 1, T = M / 8, RB = 512 / T, PITCH = P2<M>::PITCH;
   // a row of up to 256 complex values is one warp (or part of one): warp barriers only
   constexpr bool WS = T <= 32;
@@ -174,10 +174,10 @@ __global__ void __launch_bounds__(512) k_p2_rows(RowArgs a) {
     }
     // rows the mask excludes entirely are zero (cell values are finite)
     if (valid && (wrow || !rm.empty())) {
-      const float* crow = a.cell + ((long long)((z + a.oz) % U) * U + (y + a.oy) % U) * U;
+      const float* crow = a.cell + ((long long)a.fu.mod(z + a.oz) * U + a.fu.mod(y + a.oy)) * U;
       // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
-      const int cstep = (2 * T) % U;
-      int c0 = (2 * j + a.ox) % U;
+      const int cstep = a.fu.mod(2 * T);
+      int c0 = a.fu.mod(2 * j + a.ox);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int x = 2 * (j + q * T);

@@ -10,7 +10,8 @@ struct RowArgs {
   long long nrows;
   int z0;                  // absolute plane index of row 0 / N (GEN = 1)
   const float* cell;       // GEN = 1: unit cell U^3
-  int ucell, ox, oy, oz;
+  int ucell, ox, oy, oz;   // origin >= 0
+  FastDiv fu;              // division by ucell
   ShapeArgs sh;
   const float* weights;    // GEN = 1 with UR_SHAPE_WEIGHTS: full-box weights
   const float2* tw;        // table exp(-2 pi i t / N), t < N
@@ -26,7 +27,7 @@ struct GradArgs {
   const float2* tw;
   const float2* stw;       // stage twiddles of the N/2-point transform
   const float* cell;
-  int ucell, ox, oy, oz;
+  int ucell, ox, oy, oz;   // origin >= 0
   ShapeArgs sh;
   const float* weights;
   float inv_n3;

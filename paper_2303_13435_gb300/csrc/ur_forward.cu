@@ -598,6 +598,7 @@ static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long npl
     const long long np = (p0 + step <= nplanes) ? step : nplanes - p0;
     RowArgs r = ra;
     r.stw = p->stw ? p->stw + p->stw_m_off : nullptr;
+    r.fu = FastDiv((uint32_t)(ra.ucell > 0 ? ra.ucell : 1));
     r.X = X + p0 * n * H;
     r.nrows = np * n;
     r.z0 = ra.z0 + (int)p0;

@@ -175,6 +175,23 @@ def test_log_mse_grad_matches_oracle():
     assert math.isclose(float(loss.item()), L, rel_tol=1e-12)
 
 
+def test_negative_origin_is_rejected_by_every_entry_point():
+    w = mof(64, 30)
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    cell = dev(w.cell)
+    bins = api.fft_intensity_tiled(plan, cell, w.shape, ws=ws)
+    for call in (lambda: api.build_density(w.n, cell, w.shape, origin=(0, -1, 0)),
+                 lambda: api.fft_intensity_tiled(plan, cell, w.shape, origin=(0, 0, -3), ws=ws),
+                 lambda: api.backward(plan, torch.zeros(plan.nbins, dtype=torch.float64, device="cuda"), bins, cell,
+                                      w.shape, ws, origin=(-2, 0, 0))):
+        with pytest.raises(api.UrError) as e:
+            call()
+        assert e.value.status == 1 and "origin" in str(e.value)
+
+
 def test_sync_status_after_queued_work():
     w = mof(64, 30)
     rho = oracle_density(w)
