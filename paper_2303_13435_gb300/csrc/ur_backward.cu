@@ -276,10 +276,10 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
     g.stw = p->stw + p->stw_m_off;
     g.cell = cell;
     g.ucell = ucell;
-    if (origin) {
-      g.ox = origin[0];
-      g.oy = origin[1];
-      g.oz = origin[2];
+    if (origin) {  // the row kernel takes the origin reduced modulo the cell edge
+      g.ox = origin[0] % ucell;
+      g.oy = origin[1] % ucell;
+      g.oz = origin[2] % ucell;
     }
     g.sh = ur_shape_args(shape);
     g.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;

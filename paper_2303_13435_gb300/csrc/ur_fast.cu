@@ -529,7 +529,8 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
   const int cy = blockIdx.y;
   const int z = a.z0 + blockIdx.z;
   const int cz = (z + a.oz) % U;
-  const int yf = ((cy - a.oy) % U + U) % U;
+  const int yt = cy - a.oy + U;  // (cy - oy) mod U with 0 <= oy < U
+  const int yf = yt >= U ? yt - U : yt;
   const int y = yf + U * (blockIdx.x * RB + t);
   const bool valid = y < N;
   for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
@@ -586,8 +587,9 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
     const bool mzero = !wrow && rm.empty();
     // cell columns of x = 2 (j + q T): one modulo, then steps of 2T mod U; when U divides
     // 2T they are the same for every q and the dL/du sums stay in two registers
-    const int cstep = (2 * T) % U;
-    int c0 = (2 * j + a.ox) % U;
+    const int cstep = a.cstep;
+    int c0 = 2 * j + a.ox;  // reduced below: 0 <= ox < U
+    while (c0 >= U) c0 -= U;
     if (cstep == 0) {
       const int c1 = c0 + 1 == U ? 0 : c0 + 1;
       const float u0 = __ldg(crow + c0), u1 = __ldg(crow + c1);
@@ -727,6 +729,7 @@ static ur_status launch_grad_n(GradArgs a, int nplanes, cudaStream_t s) {
   int rb = 512 / T;
   if (rb > rows_per_group) rb = rows_per_group;
   a.rb = rb;
+  a.cstep = (2 * T) % U;
   const size_t smem = ur_align_up((size_t)rb * PITCH * sizeof(float2), 16) + (size_t)U * sizeof(float);
   UR_REQUIRE(smem <= 200 * 1024, "adjoint rows: cell edge %d too large", U);
   if (smem > 48 * 1024) UR_CUDA_CHECK(cudaFuncSetAttribute(k_p2_rows_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

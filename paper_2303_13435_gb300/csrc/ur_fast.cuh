@@ -27,7 +27,8 @@ struct GradArgs {
   const float2* tw;
   const float2* stw;       // stage twiddles of the N/2-point transform
   const float* cell;
-  int ucell, ox, oy, oz;   // origin >= 0
+  int ucell, ox, oy, oz;   // origin, each reduced to [0, ucell) by the host
+  int cstep;               // (N/8) mod ucell (set by the launcher)
   ShapeArgs sh;
   const float* weights;
   float inv_n3;
