@@ -311,12 +311,33 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     ky = o < M ? o : o - N;
   }
   const int c2 = kx * kx + ky * ky;
+  // z passes: the bin thresholds go to shared memory.  The adjoint, which needs the bin
+  // of every element, also stages the coarse rank table and its per-bin scales there (no
+  // gathers from global memory per element).  The forward binning needs only a few bins
+  // per column: the bins a column can reach lie between those of k^2 = c2 and c2 + M^2,
+  // read here from the full k^2 -> bin table and used after the column loads.
+  int lo_bin = 0, hi_bin = 0;
+  if (MODE == P2_Z_BIN && binning) {
+    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
+    if (threadIdx.x == 0) {
+      s_blo = 0x7fffffff;
+      s_bhi = -1;
+    }
+    if (j == 0 && valid) {
+      const int nb = a.nbins, t0 = __ldg(a.thr), tn = __ldg(a.thr + nb);
+      const int s_lo = c2, s_hi = c2 + M * M;
+      lo_bin = s_lo < t0 ? 0 : s_lo >= tn ? nb - 1 : __ldg(a.lut + s_lo);
+      hi_bin = s_hi < t0 ? 0 : s_hi >= tn ? nb - 1 : __ldg(a.lut + s_hi);
+    }
+  }
   // z passes: columns whose k^2 = kx^2 + ky^2 already lies at or beyond the closing
   // threshold reach no bin at any kz.  A block made only of such columns has nothing to
   // bin (forward, when F is not written) or only zero scales (adjoint: its output is
   // zero), so it skips the loads and the transforms.
-  if ((MODE == P2_Z_BIN && binning && !a.fout) || (MODE == P2_Z_ADJ && binning)) {
-    // every thread votes for its own column (columns past the end count as beyond)
+  const bool skip_mode = (MODE == P2_Z_BIN && binning && !a.fout) || (MODE == P2_Z_ADJ && binning);
+  if (skip_mode) {
+    // every thread votes for its own column (columns past the end count as beyond); in the
+    // forward the vote's barrier also makes the thresholds staged above visible
     const bool beyond = __syncthreads_and(!valid || c2 >= __ldg(a.thr + a.nbins));
     if (beyond) {  // uniform over the block
       // adjoint: the output columns are zero; unless the caller reads them as zeros
@@ -329,31 +350,11 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       return;
     }
   }
-  // z passes: the bin thresholds go to shared memory.  The adjoint, which needs the bin
-  // of every element, also stages the coarse rank table and its per-bin scales there (no
-  // gathers from global memory per element).  The forward binning needs only a few bins
-  // per column: the bins a column can reach lie between those of k^2 = c2 and c2 + M^2,
-  // read here from the full k^2 -> bin table and used after the column loads.
-  int lo_bin = 0, hi_bin = 0;
-  if (binning) {
+  if (MODE == P2_Z_ADJ && binning) {  // staged by the blocks that transform
     for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
-    if (MODE == P2_Z_ADJ) {
-      for (int i = threadIdx.x; i < UR_COARSE_ENTRIES / 8; i += blockDim.x)
-        reinterpret_cast<uint4*>(crs)[i] = __ldg(reinterpret_cast<const uint4*>(a.crs) + i);
-      for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) hs[i] = __ldg(a.sigma + i);
-    }
-    if (MODE == P2_Z_BIN) {
-      if (threadIdx.x == 0) {
-        s_blo = 0x7fffffff;
-        s_bhi = -1;
-      }
-      if (j == 0 && valid) {
-        const int nb = a.nbins, t0 = __ldg(a.thr), tn = __ldg(a.thr + nb);
-        const int s_lo = c2, s_hi = c2 + M * M;
-        lo_bin = s_lo < t0 ? 0 : s_lo >= tn ? nb - 1 : __ldg(a.lut + s_lo);
-        hi_bin = s_hi < t0 ? 0 : s_hi >= tn ? nb - 1 : __ldg(a.lut + s_hi);
-      }
-    }
+    for (int i = threadIdx.x; i < UR_COARSE_ENTRIES / 8; i += blockDim.x)
+      reinterpret_cast<uint4*>(crs)[i] = __ldg(reinterpret_cast<const uint4*>(a.crs) + i);
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) hs[i] = __ldg(a.sigma + i);
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
   float2 v[8];
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     }
   }
   float2* line = buf + c * PITCH;
-  if (binning) __syncthreads();  // tables (and the histogram range reset) visible
+  if (binning && (MODE == P2_Z_ADJ || !skip_mode)) __syncthreads();  // tables (and the range reset) visible
   if (MODE == P2_Z_BIN && binning && j == 0 && valid) {
     // the block's histogram range [s_blo, s_bhi] is zeroed after the transform, whose
     // barriers order it after these updates
