@@ -173,7 +173,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# algorithmic bytes per launch of each kernel (measurement); store_f: the
+# algorithmic bytes per launch of each kernel: what its pass must read and write; store_f: the
 # forward writes the half spectrum F and the adjoint reads it instead of recomputing it
 def kernel_bytes(n: int, P: int, U: int, store_f: bool = False):
     H = n // 2 + 1
