@@ -93,6 +93,23 @@ def _plane_k2(n: int, kz: int) -> np.ndarray:
     return kz * kz + (k * k)[:, None] + (k * k)[None, :]
 
 
+def voxel_sinc(n: int) -> np.ndarray:
+    """Intensity factor of one cubic voxel, prod_a sinc^2(q_a dx / 2), on the full grid [kz][ky][kx].
+
+    Sec. 2.5 (last paragraph) mentions multiplying the pattern by a voxel-sized sinc for better
+    high-Q behaviour.  Reading: the voxelised density is a sum of uniform cubes of edge dx
+    centred on the samples, so its scattering amplitude is the DFT times the cube's form factor
+    prod_a sin(q_a dx/2)/(q_a dx/2).  With q_a = 2 pi k_a/(N dx) the argument is pi k_a/N, so
+    the factor depends on the integer frequency only.
+    """
+    k = signed_freq(n).astype(np.float64)
+    a = np.pi * k / n
+    with np.errstate(invalid="ignore", divide="ignore"):
+        s = np.where(k == 0, 1.0, np.sin(a) / np.where(k == 0, 1.0, a))
+    s2 = s * s
+    return s2[:, None, None] * s2[None, :, None] * s2[None, None, :]
+
+
 def bin_intensity(I: np.ndarray, n: int, dx: float, edges: np.ndarray) -> dict:
     """Sec. 2.5 isotropic averaging of a full-grid intensity I[kz][ky][kx] into Q bins."""
     nb = len(edges) - 1
@@ -126,11 +143,16 @@ def bin_intensity(I: np.ndarray, n: int, dx: float, edges: np.ndarray) -> dict:
     return {"count": count, "sum_i": s, "mean": mean, "sem": sem, "mean_q": mean_q, "m2": m2}
 
 
-def forward(rho: np.ndarray, dx: float, edges: np.ndarray) -> dict:
-    """ED -> F (Eq. 1) -> I = |F|^2 -> binned I(Q); returns the bins plus F and I."""
+def forward(rho: np.ndarray, dx: float, edges: np.ndarray, voxel_sinc_correction: bool = False) -> dict:
+    """ED -> F (Eq. 1) -> I = |F|^2 -> binned I(Q); returns the bins plus F and I.
+
+    voxel_sinc_correction: bin I times voxel_sinc(N) (the intensity of the voxelised density
+    rather than of point samples); the returned I is then the corrected one."""
     n = rho.shape[0]
     F = dft3(rho)
     I = intensity(F)
+    if voxel_sinc_correction:
+        I = I * voxel_sinc(n)
     out = bin_intensity(I, n, dx, edges)
     out["F"] = F
     out["I"] = I

@@ -414,3 +414,145 @@ def test_log_mse_loss_gradient_matches_central_differences():
         assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(g[j]))
     # value: a plain mean of squared log ratios over the valid bins
     assert math.isclose(L, float(np.mean(np.log(mean[ok] / target[ok]) ** 2)), rel_tol=1e-12)
+
+
+def _blocky_sphere_levels(voxel_sinc_correction):
+    """ED-1 (64^3, dx 0.05 nm) of a sphere built from whole 4^3 blocks, and its 2x and 4x
+    block sums (Sec. 2.3 zoom-out) in boxes of the same physical size (32^3, 16^3).  Bin edges
+    put the level limits pi/dx on bin edges (just below, so no lattice shell sits on one)."""
+    n1, dx1 = 64, 0.05
+    b = np.arange(n1 // 4) + 0.5 - n1 // 8
+    blocks = ((b[:, None, None] ** 2 + b[None, :, None] ** 2 + b[None, None, :] ** 2) <= 16.0).astype(np.float64)
+    ed1 = np.repeat(np.repeat(np.repeat(blocks, 4, 0), 4, 1), 4, 2)
+    q3, q2, q1 = math.pi / (4 * dx1), math.pi / (2 * dx1), math.pi / dx1
+    lo = 0.9 * 2 * math.pi / (n1 * dx1)
+    edges = np.concatenate([inputs.log_edges(lo, q3 * (1 - 1e-9), 12)[:-1],
+                            inputs.log_edges(q3 * (1 - 1e-9), q2 * (1 - 1e-9), 6)[:-1],
+                            inputs.log_edges(q2 * (1 - 1e-9), q1, 6)])
+    levels = []
+    for f, n_out in [(1, 64), (2, 32), (4, 16)]:
+        ed = ed1 if f == 1 else density.zoom_out(ed1, f, n_out, out_dtype="f32").astype(np.float64)
+        ob = scatter.forward(ed, dx1 * f, edges, voxel_sinc_correction=voxel_sinc_correction)
+        levels.append({"n": n_out, "dx": dx1 * f, "count": ob["count"], "mean": ob["mean"], "sem": ob["sem"],
+                       "mean_q": ob["mean_q"]})
+    return ed1, dx1, edges, levels
+
+
+def test_merge_absolute_scale_and_seam_continuity():
+    """Sec. 2.5 merge of zoom levels, pinned without the merge's own formula.
+
+    A density made of whole 4^3 blocks is represented exactly by its 2x and 4x block sums, and
+    the unnormalised transforms of the three levels then differ, frequency by frequency, by the
+    ratio of their voxels' form factors (the geometric sum over a block equals
+    f sinc(f q dx/2)/sinc(q dx/2) per axis).  With the voxel-sinc correction the absolute
+    level curves are therefore equal in every bin below the coarser level's limit, so
+    merging all three levels must reproduce ED-1 alone there (continuity at both seams),
+    and the lowest bin must follow N_e^2 [3 (sin qR - qR cos qR)/(qR)^3]^2 (Sec. 2.2 electron
+    count, uniform-sphere form factor).  Scaling a level by N^3 instead of N^6, or by another
+    level's N, breaks both."""
+    ed1, dx1, edges, levels = _blocky_sphere_levels(True)
+    m_all = merge.merge_levels(levels, edges)
+    m_ed1 = merge.merge_levels(levels[:1], edges)
+    q2 = math.pi / (2 * dx1)
+    below = (edges[1:] <= q2) & (m_ed1["count"] > 0)
+    assert set(m_all["source"][below]) == {1, 2}
+    assert np.array_equal(m_all["count"][below], m_ed1["count"][below])
+    rel = np.abs(m_all["mean"][below] / m_ed1["mean"][below] - 1)
+    assert rel.max() < 1e-9
+    # within the SEM of either level at each seam (here: to rounding; a shell of symmetric
+    # voxels has an SEM at rounding level itself)
+    for j in np.flatnonzero(below):
+        tol = min(m_all["sem"][j], m_ed1["sem"][j]) + 1e-12 * m_ed1["mean"][j]
+        assert abs(m_all["mean"][j] - m_ed1["mean"][j]) <= tol
+    # absolute scale: electrons^2 of the unnormalised transform
+    ne = float(ed1.sum())
+    reff = (3 * ne * dx1 ** 3 / (4 * math.pi)) ** (1 / 3)
+    first = np.flatnonzero((m_all["count"] > 0) & (m_all["mean_q"] * reff < 2.4))
+    assert len(first) >= 2
+    th = inputs.sphere_target_curve(m_all["mean_q"][first], reff, ne)
+    # staircase of the blocky surface: a few percent at qR ~ 2 (the first shell: 1 %)
+    assert np.all(np.abs(m_all["mean"][first] / th - 1) < 0.03)
+    assert m_all["source"][first[0]] == 2
+
+
+def test_voxel_sinc_is_what_aligns_block_summed_levels():
+    """Without the voxel-sinc factor the 4x level of the block density is damped towards its
+    limit by the block's geometric sum (ratio ~0.45 at the axis Nyquist), and with it the
+    levels agree: the factor is prod_a sinc^2(pi k_a / N), not a look-alike."""
+    _, dx1, edges, raw = _blocky_sphere_levels(False)
+    _, _, _, cor = _blocky_sphere_levels(True)
+    q3 = math.pi / (4 * dx1)
+    sel = (edges[1:] <= q3) & (raw[0]["count"] > 0)
+    ratio_raw = raw[2]["mean"][sel] * 16.0 ** 6 / (raw[0]["mean"][sel] * 64.0 ** 6)
+    ratio_cor = cor[2]["mean"][sel] * 16.0 ** 6 / (cor[0]["mean"][sel] * 64.0 ** 6)
+    assert np.allclose(ratio_cor, 1.0, rtol=1e-9)
+    assert ratio_raw[-1] > 1.2  # the coarse point-sample transform overshoots the voxelised one near its limit
+    assert np.all(ratio_raw >= 1.0 - 1e-12)
+    # the factor itself: one at k = 0, (2/pi)^2 per axis at the Nyquist index, symmetric in k
+    s = scatter.voxel_sinc(8)
+    assert s[0, 0, 0] == 1.0
+    assert math.isclose(s[0, 0, 4], (2 / math.pi) ** 2, rel_tol=1e-15)
+    assert math.isclose(s[4, 4, 4], (2 / math.pi) ** 6, rel_tol=1e-14)
+    assert np.allclose(s[1], s[7])
+
+
+def _invvar_levels(means, sems, ns, dxs, counts=None):
+    nb = len(means[0])
+    out = []
+    for i, (m, s, n, dx) in enumerate(zip(means, sems, ns, dxs)):
+        out.append({"n": n, "dx": dx, "count": np.full(nb, 10) if counts is None else counts[i],
+                    "mean": np.asarray(m, dtype=np.float64) / float(n) ** 6,
+                    "sem": np.asarray(s, dtype=np.float64) / float(n) ** 6, "mean_q": np.full(nb, 1.0)})
+    return out
+
+
+def test_invvar_merge_is_the_maximum_likelihood_combination():
+    """Sec. 2.7 (uncertainty-optimised merge of overlapping curves): for independent Gaussian
+    errors the combined value maximises the likelihood; found here by a 1-D minimisation of
+    chi^2, independent of the closed form, and its spread over repeated draws is the SEM."""
+    from scipy.optimize import minimize_scalar
+    edges = np.array([1.0, 1.1, 1.2])
+    means = [[5.0, 7.0], [5.6, 6.1], [4.2, 9.0]]
+    sems = [[0.3, 1.0], [0.5, 0.2], [1.5, 3.0]]
+    lv = _invvar_levels(means, sems, [8, 12, 16], [0.01, 0.02, 0.04])
+    out = merge.merge_levels(lv, edges, mode="invvar")
+    for j in range(2):
+        chi2 = lambda mu: sum((means[l][j] - mu) ** 2 / sems[l][j] ** 2 for l in range(3))
+        r = minimize_scalar(chi2, bounds=(0, 20), method="bounded", options={"xatol": 1e-12})
+        assert math.isclose(out["mean"][j], r.x, rel_tol=1e-9)
+        # curvature of chi^2 = 2 / SEM^2 (second difference, independent of the weights' form)
+        h = 1e-3
+        curv = (chi2(r.x + h) - 2 * chi2(r.x) + chi2(r.x - h)) / h ** 2
+        assert math.isclose(out["sem"][j], math.sqrt(2.0 / curv), rel_tol=1e-6)
+        assert out["count"][j] == 30
+    # repeated draws: the combined estimate is unbiased and spreads by its SEM
+    rng = np.random.default_rng(4)
+    mu, sig = 3.0, np.array([0.2, 0.35, 0.9])
+    draws = []
+    for _ in range(4000):
+        m = mu + sig * rng.standard_normal(3)
+        lv = _invvar_levels([[v] for v in m], [[s] for s in sig], [8, 8, 8], [0.01, 0.02, 0.04])
+        draws.append(merge.merge_levels(lv, np.array([1.0, 1.1]), mode="invvar")["mean"][0])
+    draws = np.array(draws)
+    sem_c = 1.0 / math.sqrt(float((1.0 / sig ** 2).sum()))
+    assert abs(draws.mean() - mu) < 4 * sem_c / math.sqrt(len(draws))
+    assert abs(draws.std(ddof=1) / sem_c - 1) < 0.05
+
+
+def test_invvar_merge_respects_level_limits_and_falls_back():
+    """Levels beyond their pi/dx limit take no part; a bin where no trusted level has a usable
+    SEM takes the windows choice."""
+    edges = np.array([10.0, 11.0, 100.0, 110.0])
+    # level 0: dx 0.02 (limit 157); level 1: dx 0.2 (limit 15.7)
+    lv = _invvar_levels([[2.0, 8.0, 1.0], [3.0, 9.0, 5.0]], [[1.0, 1.0, 0.5], [1.0, 1.0, 0.5]], [16, 8],
+                        [0.02, 0.2])
+    lv[0]["sem"][1] = np.nan
+    out = merge.merge_levels(lv, edges, mode="invvar")
+    assert math.isclose(out["mean"][0], 2.5, rel_tol=1e-12) and out["count"][0] == 20
+    assert math.isclose(out["sem"][0], 1 / math.sqrt(2), rel_tol=1e-12)
+    # bin 1 (centre 33 > 15.7): only level 0 is trusted and its SEM is NaN -> windows choice
+    w = merge.merge_levels(lv, edges)
+    assert out["source"][1] == w["source"][1] == 0 and math.isclose(out["mean"][1], 8.0, rel_tol=1e-12)
+    # bin 2 (centre 105): level 1 is beyond its limit
+    assert out["source"][2] == 0 and math.isclose(out["mean"][2], 1.0, rel_tol=1e-12)
+    assert math.isclose(out["sem"][2], 0.5, rel_tol=1e-12)
