@@ -375,11 +375,7 @@ def run_ours(args):
         "metric": METRIC, "value": job_rate(n ** 3, ms_step, world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"mof512 sphere 10 nm, {n}^3 FP32 grid, {P} nonzero planes, 512 log Q bins, "
-                               "forward + adjoint (dL/d cell, dL/d mask) recomputing F along z",
-                   "grid": n, "nonzero_planes": P, "bins": 512, "cell": f"{w.ucell}^3, 2.6 nm, 60 atoms, seed 0",
-                   "l2": "inputs larger than L2 (ED slab, intermediates); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": mof_config(n, P, w.ucell, world),
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
                      if src == "measured" else "fallback 6800 GB/s", "traffic": traffic,
@@ -404,6 +400,27 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def mof_config(n: int, P: int, ucell: int, world: int) -> dict:
+    """The `config` of the default workload's JSON line (both arms)."""
+    return {"workload": f"mof512 sphere 10 nm, {n}^3 FP32 grid, {P} nonzero planes, 512 log Q bins, "
+                        "forward + adjoint (dL/d cell, dL/d mask) recomputing F along z",
+            "grid": n, "nonzero_planes": P, "bins": 512, "cell": f"{ucell}^3, 2.6 nm, 60 atoms, seed 0",
+            "l2": "inputs larger than L2 (ED slab, intermediates); no flush",
+            "parallelism": f"replicas x{world}"}
+
+
+def oracle_nonzero_planes(n: int) -> int:
+    """Planes of the default workload's density holding a nonzero voxel (oracle density, in chunks)."""
+    from oracle import density
+    w = workload(n)
+    hit = []
+    for z0 in range(0, n, 32):
+        rho = density.tile_mask_density(w.n, w.cell, w.shape.kind, w.shape.center, w.shape.size, w.shape.rot,
+                                        z_begin=z0, z_count=min(32, n - z0))
+        hit.extend((z0 + i) for i in np.flatnonzero(rho.any(axis=(1, 2))))
+    return int(hit[-1] - hit[0] + 1) if hit else 0
 
 
 def oracle_step(n: int):
@@ -432,19 +449,25 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
-    n = 256  # bounded sample of the 512^3 workload: same cell, dx and bins, half the box and sphere
+    # the same workload and config as the GPU arm; each timed step is a bounded sample of it:
+    # the oracle's forward + adjoint on the 256^3 grid of the same cell, dx, bins and a sphere
+    # scaled with the box (5 nm), so that warm-up plus K steps finish within minutes
+    full = args.n
+    sample_n = 256 if full > 256 else full
+    P = oracle_nonzero_planes(full)
     for _ in range(args.warmup):
-        oracle_step(n)
-    times = [oracle_step(n) for _ in range(args.steps)]
+        oracle_step(sample_n)
+    times = [oracle_step(sample_n) for _ in range(args.steps)]
     ms = 1e3 * sum(times) / len(times)
-    v = n ** 3 / (ms * 1e-3)
+    v = sample_n ** 3 / (ms * 1e-3)
+    sample = (f"{args.steps} forward + adjoint steps of the FP64 numpy oracle on the {sample_n}^3 grid of the same "
+              f"cell, dx and bins ({sample_n * 10.0 / 512:g} nm sphere), {ms / 1e3:.1f} s each; voxels/s counts "
+              f"that grid's voxels")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "mof sphere, 256^3 FP64 oracle sample of the 512^3 workload (5 nm sphere), "
-                                  "512 log Q bins, forward + adjoint", "grid": n, "bins": 512},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} oracle steps on the 256^3 grid"},
+           "config": dict(mof_config(full, P, 64, args.gpus), sample_grid=sample_n),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -595,7 +618,7 @@ def run_merge3(args):
     ws = [p.workspace(api.UR_WS_FORWARD) for p in plans]
     bins = [api.new_bins(p) for p in plans]
     ns = [n for _, n, _, _ in levels]
-    qmax = [math.pi / dx for _, _, dx, _ in levels]
+    dxs = [dx for _, _, dx, _ in levels]
     merged = torch.empty((5, len(ed1w.edges) - 1), dtype=torch.float64, device="cuda")
 
     def step():
@@ -604,7 +627,7 @@ def run_merge3(args):
             if f > 1:
                 api.zoom_density(ed1, f, n, out_dtype="f16", out=ed)
             api.fft_intensity(plan, ed[z0:z0 + nz], bins=b, ws=w_)
-        api.merge(bins, ns, qmax, edges_d, out=merged)
+        api.merge(bins, ns, dxs, edges_d, out=merged)
 
     ms = _timed(step, args.steps, args.warmup)
     out_np = merged.cpu().numpy()

@@ -217,9 +217,14 @@ ur_status ur_fft_intensity_tiled(const ur_plan* plan, const float* cell, int32_t
  *   - All calls share the one array, which keeps the last call's contents:
  *     calls whose work overlaps on the GPU (two streams at once) race and
  *     give wrong results; serialise them.
- *   ed: device planes [z0, z0+nz), ed_dtype; bins: device double[6][B]. */
+ *   - The current device must be the one the plan was created on
+ *     (UR_ERR_INVALID otherwise).  The UR_FAULT site "fft_intensity" covers
+ *     this call too.
+ *   ed: device planes [z0, z0+nz), ed_dtype; bins: device double[6][B] (required). */
 #define UR_NOALLOC_SCRATCH_BYTES (64u << 20)
 ur_status ur_fft_intensity_noalloc(const ur_plan* plan, const void* ed, double* bins, void* stream);
+/* Size of that scratch array in bytes, as built into the library (host only). */
+size_t ur_noalloc_scratch_bytes(void);
 
 /* Sec. 2.5 binning of a stored half-spectrum intensity I[kz][ky][kx]
  * (device float32, N*N*(N/2+1), Eq. 1 normalised); kx in (0, N/2) weighs 2
@@ -228,23 +233,39 @@ ur_status ur_bin_q(const ur_plan* plan, const float* intensity_half, double* bin
                    size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
- * ur_merge (Sec. 2.5 last paragraph; Fig. 2 caption).
+ * ur_merge (Sec. 2.5 last paragraph; Fig. 2 caption; Sec. 2.7 for the
+ * uncertainty-weighted combination of overlapping curves).
  *   nlev        number of levels (1..8)
  *   level_bins  host array of nlev device pointers, each double[UR_BIN_FIELDS][B]
  *               binned over the same edges
  *   level_n     host int32[nlev], grid edge of each level (intensity scale N^6)
- *   level_qmax  host double[nlev], upper |Q| of each level's validity window
- *               (pi/dx_level for the Q_max/2 artefact limit with Q_max = 2 pi/dx)
+ *   level_dx    host double[nlev], voxel edge of each level (nm); the library
+ *               trusts a level up to Q_max/2 = pi/dx (ur_level_qmax), the
+ *               artefact limit of the Fig. 2 caption with Q_max = 2 pi/dx
  *   edges       device double[B+1] (the edges all levels were binned on)
+ *   mode        UR_MERGE_WINDOWS: disjoint windows.  Levels are ordered by
+ *               their limit; the one with the smallest limit covers [0, its
+ *               limit), each next one [previous limit, its limit), the last
+ *               one closed.  Each output bin takes the level whose window
+ *               holds sqrt(e_j e_j+1).
+ *               UR_MERGE_INVVAR: each output bin combines every level trusted
+ *               at sqrt(e_j e_j+1) that has voxels and a finite positive SEM
+ *               there, with weights 1/SEM^2 (absolute units): mean = sum w m /
+ *               sum w, SEM = (sum w)^(-1/2), count and sum |Q| added; bins with
+ *               no such level fall back to the windows choice.
  *   out         device double[5][B]: mean, sem (absolute units, electrons^2),
- *               count, mean |Q|, source level (-1: none).
- * Levels are ordered by level_qmax; the one with the smallest limit covers
- * [0, its limit), each next one [previous limit, its limit), the last one
- * closed.  Each output bin takes the level whose window holds sqrt(e_j e_j+1).
+ *               count, mean |Q|, source level (-1: none; INVVAR: the level of
+ *               largest weight).
+ * Errors: UR_ERR_INVALID for nlev outside [1, 8], null pointers, N <= 0, a dx
+ * that is not finite and positive, or an unknown mode.
  * ------------------------------------------------------------------------- */
+enum { UR_MERGE_WINDOWS = 0, UR_MERGE_INVVAR = 1 };
 ur_status ur_merge(int32_t nlev, const double* const* level_bins, const int32_t* level_n,
-                   const double* level_qmax, const double* edges, int32_t nbins, double* out,
+                   const double* level_dx, const double* edges, int32_t nbins, int32_t mode, double* out,
                    void* stream);
+/* The upper |Q| (nm^-1) up to which ur_merge trusts a level of voxel edge dx: pi/dx
+ * (host only; 0 for a dx that is not finite and positive). */
+double ur_level_qmax(double dx);
 
 /* ---------------------------------------------------------------------------
  * ur_backward: adjoint of ur_build_density + ur_fft_intensity for a loss L

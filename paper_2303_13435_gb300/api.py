@@ -7,7 +7,6 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np
@@ -59,8 +58,10 @@ SIGNATURES = {
     "ur_fft_intensity_tiled": (_i32, [_vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp, _vp,
                                       _sz, _vp]),
     "ur_fft_intensity_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
+    "ur_noalloc_scratch_bytes": (_sz, []),
     "ur_bin_q": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
-    "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _vp, _vp]),
+    "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _i32, _vp, _vp]),
+    "ur_level_qmax": (C.c_double, [C.c_double]),
     "ur_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
                            _vp, _sz, _vp]),
     "ur_set_timing": (None, [_i32]),
@@ -196,6 +197,21 @@ class Plan:
     def workspace(self, what: int = UR_WS_FORWARD, device="cuda") -> torch.Tensor:
         return torch.empty(self.workspace_size(what), dtype=torch.uint8, device=device)
 
+    def claim_workspace(self, what: int = UR_WS_FORWARD, device="cuda") -> tuple[torch.Tensor, int]:
+        """The plan's own workspace, allocated once (grown when `what` needs more) and reused by
+        every claim.  Returns (workspace, generation); the generation changes at each claim, so
+        a holder can tell whether someone else has written the workspace since its claim."""
+        need = self.workspace_size(what)
+        ws = getattr(self, "_ws", None)
+        if ws is None or ws.numel() < need or ws.device != torch.device(device):
+            ws = torch.empty(need, dtype=torch.uint8, device=device)
+            self._ws = ws
+        self._ws_gen = getattr(self, "_ws_gen", 0) + 1
+        return ws, self._ws_gen
+
+    def workspace_generation(self) -> int:
+        return getattr(self, "_ws_gen", 0)
+
     def close(self):
         if getattr(self, "_h", None):
             lib().ur_plan_destroy(self._h)
@@ -289,12 +305,14 @@ def sync_status(stream=None) -> None:
     _check("ur_sync_status", lib().ur_sync_status(_stream(stream)))
 
 
-NOALLOC_SCRATCH_BYTES = 64 << 20
+def noalloc_scratch_bytes() -> int:
+    """Size of the library's built-in scratch array used by fft_intensity_noalloc."""
+    return int(lib().ur_noalloc_scratch_bytes())
 
 
 def fft_intensity_noalloc(plan: Plan, ed: torch.Tensor, bins: torch.Tensor, stream=None) -> torch.Tensor:
     """ur_fft_intensity without a workspace, for callers that must not allocate while
-    running: the intermediate sits in the library's built-in 64 MiB scratch array.
+    running: the intermediate sits in the library's built-in scratch array (noalloc_scratch_bytes()).
     `bins` must be preallocated by the caller; calls that overlap on the GPU race."""
     _check("ur_fft_intensity_noalloc", lib().ur_fft_intensity_noalloc(plan.handle, _ptr(ed), _ptr(bins),
                                                                       _stream(stream)))
@@ -308,18 +326,29 @@ def bin_q(plan: Plan, I_half: torch.Tensor, bins: torch.Tensor | None = None, st
     return bins
 
 
-def merge(level_bins: list, level_n: list, level_qmax: list, edges_dev: torch.Tensor, out: torch.Tensor | None = None,
-          stream=None) -> torch.Tensor:
-    """Sec. 2.5 merge of level curves into absolute units; out[5, B] = mean, sem, count, mean Q, source."""
+MERGE_MODES = {"windows": 0, "invvar": 1}
+
+
+def merge(level_bins: list, level_n: list, level_dx: list, edges_dev: torch.Tensor, out: torch.Tensor | None = None,
+          mode: str = "windows", stream=None) -> torch.Tensor:
+    """Sec. 2.5 merge of level curves into absolute units; out[5, B] = mean, sem, count, mean Q, source.
+
+    level_dx: voxel edge of each level (nm); the library derives each level's limit from it."""
     nlev = len(level_bins)
     nb = edges_dev.numel() - 1
     if out is None:
         out = torch.empty((5, nb), dtype=torch.float64, device=edges_dev.device)
     ptrs = (C.c_void_p * nlev)(*[b.data_ptr() for b in level_bins])
     ns = (C.c_int32 * nlev)(*[int(v) for v in level_n])
-    qs = (C.c_double * nlev)(*[float(v) for v in level_qmax])
-    _check("ur_merge", lib().ur_merge(nlev, ptrs, ns, qs, _ptr(edges_dev), nb, _ptr(out), _stream(stream)))
+    dxs = (C.c_double * nlev)(*[float(v) for v in level_dx])
+    _check("ur_merge", lib().ur_merge(nlev, ptrs, ns, dxs, _ptr(edges_dev), nb, MERGE_MODES[mode], _ptr(out),
+                                      _stream(stream)))
     return out
+
+
+def level_qmax(dx: float) -> float:
+    """The |Q| up to which ur_merge trusts a level of voxel edge dx (computed by the library)."""
+    return float(lib().ur_level_qmax(float(dx)))
 
 
 def backward(plan: Plan, dl_dmean: torch.Tensor, fwd_bins: torch.Tensor, cell: torch.Tensor, shape, ws: torch.Tensor,
@@ -429,6 +458,3 @@ def header_symbols() -> list[str]:
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(ur_[a-z0-9_]+)\s*\(", txt)))
 
-
-def qmax_nyquist(dx: float) -> float:
-    return math.pi / dx

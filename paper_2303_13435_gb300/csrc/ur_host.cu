@@ -457,42 +457,81 @@ extern "C" size_t ur_workspace_size(const ur_plan* p, int32_t what) {
 }
 
 // ---------------------------------------------------------------------------
-// Merge (Sec. 2.5 last paragraph): one thread per output bin.
+// Merge (Sec. 2.5 last paragraph; Fig. 2 caption; Sec. 2.7 for the
+// uncertainty-weighted combination): one thread per output bin.
 // ---------------------------------------------------------------------------
 #define UR_MAX_LEVELS 8
 struct MergeArgs {
-  const double* bins[UR_MAX_LEVELS];
-  double scale[UR_MAX_LEVELS];  // N^6
-  double qlo[UR_MAX_LEVELS];    // window lower edge, in window order
-  double qhi[UR_MAX_LEVELS];
-  int order[UR_MAX_LEVELS];     // level index of the t-th window
-  int nlev;
+  const double* bins[UR_MAX_LEVELS];  // in window order (coarsest level first)
+  double scale[UR_MAX_LEVELS];        // N^6
+  double qlo[UR_MAX_LEVELS];          // window lower edge, in window order
+  double qhi[UR_MAX_LEVELS];          // level limit pi/dx
+  int order[UR_MAX_LEVELS];           // caller's level index of the t-th window
+  int pos[UR_MAX_LEVELS];             // window position of the caller's level i
+  int nlev, mode;
 };
+
+// Q_max/2 artefact limit of a level (Fig. 2 caption) with Q_max = 2 pi/dx the sampling frequency
+extern "C" double ur_level_qmax(double dx) { return (dx > 0 && isfinite(dx)) ? M_PI / dx : 0.0; }
 
 __global__ void k_merge(MergeArgs a, const double* __restrict__ edges, int nb, double* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const double c = sqrt(edges[j] * edges[j + 1]);
-  int pick = -1;
-  for (int t = 0; t < a.nlev; ++t) {
-    const bool last = t == a.nlev - 1;
-    if ((a.qlo[t] <= c && c < a.qhi[t]) || (last && c == a.qhi[t])) {
-      pick = t;
-      break;
-    }
-  }
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   double mean = nan, sem = nan, cnt = 0.0, q = nan, src = -1.0;
-  if (pick >= 0) {
-    const double* b = a.bins[pick];
-    const double n = b[UR_BIN_COUNT * nb + j];
-    if (n > 0) {
-      const double s = a.scale[pick];
-      mean = b[UR_BIN_MEAN * nb + j] * s;
-      sem = b[UR_BIN_SEM * nb + j] * s;
-      cnt = n;
-      q = b[UR_BIN_SUM_Q * nb + j] / n;
-      src = (double)a.order[pick];
+  bool done = false;
+  if (a.mode == UR_MERGE_INVVAR) {
+    // every level trusted at the bin centre with voxels and a usable SEM, weight 1/SEM^2,
+    // accumulated in the caller's level order
+    double sw = 0.0, swm = 0.0, sn = 0.0, sq = 0.0, best_w = -1.0;
+    int best = -1;
+    for (int i = 0; i < a.nlev; ++i) {
+      const int t = a.pos[i];
+      const double* b = a.bins[t];
+      const double n = b[UR_BIN_COUNT * nb + j];
+      if (c > a.qhi[t] || !(n > 0)) continue;
+      const double s_abs = b[UR_BIN_SEM * nb + j] * a.scale[t];
+      if (!(isfinite(s_abs) && s_abs > 0)) continue;
+      const double w = 1.0 / (s_abs * s_abs);
+      sw += w;
+      swm += w * (b[UR_BIN_MEAN * nb + j] * a.scale[t]);
+      sn += n;
+      sq += b[UR_BIN_SUM_Q * nb + j];
+      if (w > best_w) {
+        best_w = w;
+        best = i;
+      }
+    }
+    if (best >= 0) {
+      mean = swm / sw;
+      sem = 1.0 / sqrt(sw);
+      cnt = sn;
+      q = sq / sn;
+      src = (double)best;
+      done = true;
+    }
+  }
+  if (!done) {
+    int pick = -1;
+    for (int t = 0; t < a.nlev; ++t) {
+      const bool last = t == a.nlev - 1;
+      if ((a.qlo[t] <= c && c < a.qhi[t]) || (last && c == a.qhi[t])) {
+        pick = t;
+        break;
+      }
+    }
+    if (pick >= 0) {
+      const double* b = a.bins[pick];
+      const double n = b[UR_BIN_COUNT * nb + j];
+      if (n > 0) {
+        const double s = a.scale[pick];
+        mean = b[UR_BIN_MEAN * nb + j] * s;
+        sem = b[UR_BIN_SEM * nb + j] * s;
+        cnt = n;
+        q = b[UR_BIN_SUM_Q * nb + j] / n;
+        src = (double)a.order[pick];
+      }
     }
   }
   out[0 * nb + j] = mean;
@@ -503,23 +542,27 @@ __global__ void k_merge(MergeArgs a, const double* __restrict__ edges, int nb, d
 }
 
 extern "C" ur_status ur_merge(int32_t nlev, const double* const* level_bins, const int32_t* level_n,
-                              const double* level_qmax, const double* edges, int32_t nbins, double* out,
+                              const double* level_dx, const double* edges, int32_t nbins, int32_t mode, double* out,
                               void* stream) {
   UR_REQUIRE(nlev >= 1 && nlev <= UR_MAX_LEVELS, "ur_merge: nlev %d outside [1, %d]", nlev, UR_MAX_LEVELS);
-  UR_REQUIRE(level_bins && level_n && level_qmax && edges && out, "ur_merge: null argument");
+  UR_REQUIRE(level_bins && level_n && level_dx && edges && out, "ur_merge: null argument");
   UR_REQUIRE(nbins >= 1, "ur_merge: nbins must be positive");
+  UR_REQUIRE(mode == UR_MERGE_WINDOWS || mode == UR_MERGE_INVVAR, "ur_merge: unknown mode %d", mode);
   MergeArgs a;
   memset(&a, 0, sizeof a);
   a.nlev = nlev;
+  a.mode = mode;
   int idx[UR_MAX_LEVELS];
+  double qmax[UR_MAX_LEVELS];
   for (int i = 0; i < nlev; ++i) {
     UR_REQUIRE(level_bins[i], "ur_merge: level %d has no bins", i);
-    UR_REQUIRE(level_n[i] > 0 && level_qmax[i] > 0, "ur_merge: level %d has a bad size or window", i);
+    UR_REQUIRE(level_n[i] > 0 && level_dx[i] > 0 && isfinite(level_dx[i]), "ur_merge: level %d has a bad size or dx", i);
+    qmax[i] = ur_level_qmax(level_dx[i]);
     idx[i] = i;
   }
   // windows ordered by their upper limit (coarsest level first); stable
   for (int i = 1; i < nlev; ++i)
-    for (int k = i; k > 0 && level_qmax[idx[k]] < level_qmax[idx[k - 1]]; --k) {
+    for (int k = i; k > 0 && qmax[idx[k]] < qmax[idx[k - 1]]; --k) {
       int t = idx[k];
       idx[k] = idx[k - 1];
       idx[k - 1] = t;
@@ -531,9 +574,10 @@ extern "C" ur_status ur_merge(int32_t nlev, const double* const* level_bins, con
     double nn = (double)level_n[i];
     a.scale[t] = nn * nn * nn * nn * nn * nn;
     a.qlo[t] = lo;
-    a.qhi[t] = level_qmax[i];
+    a.qhi[t] = qmax[i];
     a.order[t] = i;
-    lo = level_qmax[i];
+    a.pos[i] = t;
+    lo = qmax[i];
   }
   cudaStream_t s = (cudaStream_t)stream;
   k_merge<<<(nbins + 127) / 128, 128, 0, s>>>(a, edges, nbins, out);

@@ -33,10 +33,14 @@ static __device__ __align__(256) unsigned char g_ur_noalloc_scratch[UR_NOALLOC_S
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[UR_NOALLOC_MAX_DEVICES];
 
-static ur_status noalloc_scratch(void** out) {
+static ur_status noalloc_scratch(const ur_plan* p, void** out) {
   int dev = 0;
   UR_CUDA_CHECK(cudaGetDevice(&dev));
   UR_REQUIRE(dev >= 0 && dev < UR_NOALLOC_MAX_DEVICES, "ur_fft_intensity_noalloc: device %d out of range", dev);
+  // the plan's tables live on the device it was created on; the scratch array used must be
+  // that device's too
+  UR_REQUIRE(dev == p->device, "ur_fft_intensity_noalloc: current device %d is not the plan's device %d", dev,
+             p->device);
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -52,16 +56,19 @@ static ur_status noalloc_scratch(void** out) {
   return UR_OK;
 }
 
+extern "C" size_t ur_noalloc_scratch_bytes(void) { return (size_t)UR_NOALLOC_SCRATCH_BYTES; }
+
 extern "C" ur_status ur_fft_intensity_noalloc(const ur_plan* p, const void* ed, double* bins, void* stream) {
-  UR_REQUIRE(p && ed, "ur_fft_intensity_noalloc: null argument");
+  UR_REQUIRE(p && ed && bins, "ur_fft_intensity_noalloc: null argument");
   const size_t need = ur_workspace_size(p, UR_WS_FORWARD);
   UR_REQUIRE(need <= (size_t)UR_NOALLOC_SCRATCH_BYTES,
              "ur_fft_intensity_noalloc: this plan needs %zu bytes of intermediate (nz * N * (N/2+1) * 8); the built-in "
              "scratch holds %zu bytes -- use ur_fft_intensity with a workspace",
              need, (size_t)UR_NOALLOC_SCRATCH_BYTES);
   UR_REQUIRE(((uintptr_t)ed % 8) == 0, "ur_fft_intensity_noalloc: ed must be 8-byte aligned");
+  UR_TRY(ur_fault_point("fft_intensity"));
   void* scratch = nullptr;
-  UR_TRY(noalloc_scratch(&scratch));
+  UR_TRY(noalloc_scratch(p, &scratch));
   cudaStream_t s = (cudaStream_t)stream;
   float2* X = (float2*)scratch;
   UR_TRY(ur_plane_pass(p, ed, p->nz, X, s));

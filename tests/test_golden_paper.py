@@ -68,7 +68,7 @@ def test_q_range_of_the_three_levels():
     # frequency 2 pi / dx, and it is the limit the library and the workloads use
     q_ny = float(scatter.q_of_k2(np.array([(n1 // 2) ** 2], dtype=np.int64), n1, dx1)[0])
     assert q_ny == pytest.approx(G["artefact_fraction_of_qmax"] * 2.0 * math.pi / dx1, rel=1e-12)
-    assert api.qmax_nyquist(dx1) == pytest.approx(q_ny, rel=1e-12)
+    assert api.level_qmax(dx1) == pytest.approx(q_ny, rel=1e-12)
     assert inputs.nyquist_q(dx1) == pytest.approx(q_ny, rel=1e-12)
     # the printed reach lies inside ED-1's trusted range, and not by a factor of 2 pi
     assert G["q_high_approx_per_nm"] < q_ny < 2.0 * G["q_high_approx_per_nm"]

@@ -78,9 +78,32 @@ def test_autograd_directional_derivative_on_the_gpu():
     assert math.isclose(fd, an, rel_tol=1e-2), (fd, an)
 
 
+def test_autograd_reuses_the_plan_workspace_and_survives_interleaved_forwards():
+    """One workspace per plan for every forward; a backward that runs after another forward
+    wrote that workspace restores its own intermediate first and gets the same gradient."""
+    w = _small_workload()
+    plan = api.Plan(w.n, w.dx, w.edges)
+    base = torch.from_numpy(w.cell).cuda()
+
+    def grad_of(cell_t, pl, interleave=None):
+        c = cell_t.clone().requires_grad_(True)
+        mean = binned_intensity(c, pl, w.shape)
+        if interleave is not None:
+            binned_intensity(interleave, pl, w.shape)   # claims and overwrites the workspace
+        torch.nan_to_num(mean).sum().backward()
+        return c.grad.clone()
+
+    binned_intensity(base, plan, w.shape)
+    ws_first = plan._ws.data_ptr()
+    g_inter = grad_of(base, plan, interleave=base * 1.7)
+    assert plan._ws.data_ptr() == ws_first
+    g_alone = grad_of(base, api.Plan(w.n, w.dx, w.edges))
+    assert normwise(g_inter.cpu().numpy(), g_alone.cpu().numpy()) <= 1e-6
+
+
 def _levels_gpu(ed1_dev, n1, dx1, zooms, edges):
-    """Transform every level on common edges; returns (bins tensors, N list, qmax list, box totals)."""
-    out_bins, ns, qmax = [], [], []
+    """Transform every level on common edges; returns (bins tensors, N list, dx list, box totals)."""
+    out_bins, ns, dxs = [], [], []
     lv = [(ed1_dev, n1, dx1)]
     for f, n_out in zooms:
         lv.append((api.zoom_density(ed1_dev, f, n_out, out_dtype="f16"), n_out, dx1 * f))
@@ -90,8 +113,8 @@ def _levels_gpu(ed1_dev, n1, dx1, zooms, edges):
         plan = api.Plan(n, dx, edges, z0=z0, nz=z1 - z0 + 1, ed_dtype="f16")
         out_bins.append(api.fft_intensity(plan, ed[z0:z1 + 1].contiguous()))
         ns.append(n)
-        qmax.append(math.pi / dx)
-    return out_bins, ns, qmax, lv
+        dxs.append(dx)
+    return out_bins, ns, dxs, lv
 
 
 def test_three_level_merge_matches_oracle_reduced():
@@ -102,8 +125,8 @@ def test_three_level_merge_matches_oracle_reduced():
                                        nbins=150, qlo=0.05, qhi=150.0)
     edges = ed1w.edges
     ed1 = oracle_density(ed1w, out_dtype="f16")
-    bins, ns, qmax, lv = _levels_gpu(torch.from_numpy(ed1).cuda(), n1, ed1w.dx, [(4, 128), (16, 128)], edges)
-    out = api.merge(bins, ns, qmax, torch.from_numpy(edges).cuda()).cpu().numpy()
+    bins, ns, dxs, lv = _levels_gpu(torch.from_numpy(ed1).cuda(), n1, ed1w.dx, [(4, 128), (16, 128)], edges)
+    out = api.merge(bins, ns, dxs, torch.from_numpy(edges).cuda()).cpu().numpy()
     # oracle levels
     olv = []
     for (f, n_out), gb in zip([(1, n1), (4, 128), (16, 128)], bins):
@@ -136,8 +159,8 @@ def test_three_level_merge_full_size():
     ed1w, zooms = inputs.cube_merge_levels()
     cell = torch.from_numpy(ed1w.cell).cuda()
     ed1 = api.build_density(ed1w.n, cell, ed1w.shape, out_dtype="f16")
-    bins, ns, qmax, lv = _levels_gpu(ed1, ed1w.n, ed1w.dx, [(f, n) for f, n, _ in zooms], ed1w.edges)
-    out = api.merge(bins, ns, qmax, torch.from_numpy(ed1w.edges).cuda()).cpu().numpy()
+    bins, ns, dxs, lv = _levels_gpu(ed1, ed1w.n, ed1w.dx, [(f, n) for f, n, _ in zooms], ed1w.edges)
+    out = api.merge(bins, ns, dxs, torch.from_numpy(ed1w.edges).cuda()).cpu().numpy()
     src = out[4].astype(np.int64)
     assert set(np.unique(src[src >= 0])) == {0, 1, 2}
     used = src >= 0

@@ -251,7 +251,7 @@ def test_merge_matches_oracle():
         b[4] = lv["mean"]
         b[5] = lv["sem"]
         dev_bins.append(dev(b))
-    out = api.merge(dev_bins, [lv["n"] for lv in levels], [math.pi / lv["dx"] for lv in levels], dev(edges))
+    out = api.merge(dev_bins, [lv["n"] for lv in levels], [lv["dx"] for lv in levels], dev(edges))
     o = out.cpu().numpy()
     assert np.array_equal(o[4].astype(np.int64), want["source"])
     assert np.array_equal(o[2].astype(np.int64), want["count"])
@@ -260,6 +260,52 @@ def test_merge_matches_oracle():
     assert np.array_equal(o[1][ok], want["sem"][ok])
     assert np.allclose(o[3][ok], want["mean_q"][ok], rtol=1e-15)
     assert np.all(np.isnan(o[0][~ok]))
+    # uncertainty-weighted combination where levels overlap (Sec. 2.7)
+    want = omerge.merge_levels(levels, edges, mode="invvar")
+    o = api.merge(dev_bins, [lv["n"] for lv in levels], [lv["dx"] for lv in levels], dev(edges),
+                  mode="invvar").cpu().numpy()
+    assert np.array_equal(o[4].astype(np.int64), want["source"])
+    assert np.array_equal(o[2].astype(np.int64), want["count"])
+    ok = want["source"] >= 0
+    assert np.allclose(o[0][ok], want["mean"][ok], rtol=1e-13, atol=0)
+    assert np.allclose(o[1][ok], want["sem"][ok], rtol=1e-13, atol=0)
+    assert np.allclose(o[3][ok], want["mean_q"][ok], rtol=1e-13)
+    assert np.all(np.isnan(o[0][~ok]))
+
+
+def _oracle_counts(n, dx, edges):
+    """n_j of the oracle's binning (float64 |Q| of every integer k of the grid), plane by plane."""
+    nb = len(edges) - 1
+    cnt = np.zeros(nb, dtype=np.int64)
+    for kz in scatter.signed_freq(n):
+        j = scatter.bin_of_q(scatter.q_of_k2(scatter._plane_k2(n, int(kz)), n, dx), edges).ravel()
+        cnt += np.bincount(j[j >= 0], minlength=nb)
+    return cnt
+
+
+@pytest.mark.parametrize("n,nbins", [(512, 512), (256, 200), (126, 96), (100, 80)])
+def test_single_voxel_bins_every_voxel_exactly(n, nbins):
+    """The data pass's bin index of every voxel, not the plan's geometry: a unit voxel at the
+    origin transforms to F~ = 1 at every k (exactly, in FP32), so the binned sum of I is the
+    number of voxels the fused z-pass walk put in each bin.  Power-of-two grids (compile-time
+    kernels) make every term a power of two and the sum exact; the runtime-radix grids carry
+    one FP32 rounding of 1/N^3 per term and at most 1e-6 relative error per bin, below half a
+    voxel for these counts."""
+    dx = 0.04
+    edges = inputs.log_edges(2 * math.pi / (n * dx), math.pi / dx, nbins)
+    ed = torch.zeros((1, n, n), dtype=torch.float32, device="cuda")
+    ed[0, 0, 0] = 1.0
+    plan = api.Plan(n, dx, edges, z0=0, nz=1)
+    gb = api.fft_intensity(plan, ed).cpu().numpy()
+    want = _oracle_counts(n, dx, edges)
+    assert np.array_equal(gb[0].astype(np.int64), want)
+    per_voxel = float(np.float32(1.0 / n ** 3)) * n ** 3   # the kernel's FP32 scale times N^3
+    voxels = gb[1] * float(n) ** 6 / per_voxel
+    if n & (n - 1) == 0:
+        assert np.array_equal(voxels, want.astype(np.float64))
+    else:
+        assert np.max(np.abs(voxels - want)) < 0.25
+        assert np.array_equal(np.rint(voxels).astype(np.int64), want)
 
 
 # ---------------------------------------------------------------------------
