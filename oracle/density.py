@@ -78,6 +78,60 @@ def tiled_cell(n: int, cell: np.ndarray, origin=(0, 0, 0), z_begin: int = 0, z_c
     return cell[np.ix_(iz, iy, ix)].astype(np.float32)
 
 
+def rotated_cell(n: int, cell: np.ndarray, lat_rot, lat_offset, z_begin: int = 0, z_count: int | None = None,
+                 center=None) -> np.ndarray:
+    """The unit cell sampled on a rotated lattice with periodic wrap, float32 [z][y][x].
+
+    Sec. 2.3 (first paragraph) interpolates the reduced cell over rotated planes with
+    scipy's map_coordinates in grid-wrap mode, the cell repeating outside its bounds, to
+    give the crystal an orientation (the way to polycrystalline grains).  Reading: the
+    sample point of voxel x, in cell-voxel units, is p = R (x - c) + q, with R the lattice
+    rotation, c the rotation centre (the particle centre) and q = c + o an offset; the
+    value is the trilinear interpolation (order 1) of the periodic cell at p.  Every step
+    is float32 with each product, sum and difference rounded separately, in this order:
+      d_b = x_b - c_b;  p_a = ((R[a][0] d_0 + R[a][1] d_1) + R[a][2] d_2) + q_a
+      i = floor(p), f = p - i (exact), lerp(a, b, f) = a + f (b - a)
+      along x, then y, then z over the 8 neighbours (i + {0,1}) mod U.
+    (x, y, z) = (index 2, 1, 0) of the [z][y][x] arrays, as for the shape masks.
+    """
+    if z_count is None:
+        z_count = n - z_begin
+    u = cell.shape[0]
+    cl = np.asarray(cell, dtype=np.float32)
+    r = np.asarray(lat_rot, dtype=np.float32).reshape(3, 3)
+    c = np.asarray(center if center is not None else (n // 2, n // 2, n // 2), dtype=np.float32)
+    q = np.asarray(lat_offset, dtype=np.float32)
+    dx = (np.arange(n, dtype=np.float32) - c[0])[None, None, :]
+    dy = (np.arange(n, dtype=np.float32) - c[1])[None, :, None]
+    dz = (np.arange(z_begin, z_begin + z_count, dtype=np.float32) - c[2])[:, None, None]
+    p = []
+    for a in range(3):
+        pa = (r[a, 0] * dx + r[a, 1] * dy)
+        pa = pa + r[a, 2] * dz
+        p.append((pa + q[a]).astype(np.float32))
+    i = [np.floor(pa) for pa in p]
+    f = [(pa - ia).astype(np.float32) for pa, ia in zip(p, i)]
+    ii = [np.mod(ia.astype(np.int64), u) for ia in i]
+    ij = [np.mod(ia + 1, u) for ia in ii]
+
+    def lerp(a0, a1, t):
+        return (a0 + t * (a1 - a0)).astype(np.float32)
+
+    def g(iz, iy, ix):
+        return cl[iz, iy, ix]
+
+    x0, x1 = ii[0], ij[0]
+    y0, y1 = ii[1], ij[1]
+    z0, z1 = ii[2], ij[2]
+    c00 = lerp(g(z0, y0, x0), g(z0, y0, x1), f[0])
+    c01 = lerp(g(z0, y1, x0), g(z0, y1, x1), f[0])
+    c10 = lerp(g(z1, y0, x0), g(z1, y0, x1), f[0])
+    c11 = lerp(g(z1, y1, x0), g(z1, y1, x1), f[0])
+    c0 = lerp(c00, c01, f[1])
+    c1 = lerp(c10, c11, f[1])
+    return lerp(c0, c1, f[2]).astype(np.float32)
+
+
 def mask_values(n: int, kind: int, center=(0, 0, 0), size=0.0, rot=np.eye(3), weights=None,
                 z_begin: int = 0, z_count: int | None = None) -> np.ndarray:
     if kind == WEIGHTS:
@@ -89,9 +143,15 @@ def mask_values(n: int, kind: int, center=(0, 0, 0), size=0.0, rot=np.eye(3), we
 
 def tile_mask_density(n: int, cell: np.ndarray, kind: int, center=(0, 0, 0), size=0.0, rot=np.eye(3),
                       origin=(0, 0, 0), weights=None, out_dtype: str = "f32",
-                      z_begin: int = 0, z_count: int | None = None) -> np.ndarray:
-    """ED-1 for planes [z_begin, z_begin + z_count): rho = fl32(u(x mod U) * m(x)), optionally to FP16."""
-    u = tiled_cell(n, cell, origin, z_begin, z_count)
+                      z_begin: int = 0, z_count: int | None = None, lattice=None) -> np.ndarray:
+    """ED-1 for planes [z_begin, z_begin + z_count): rho = fl32(u(x mod U) * m(x)), optionally to FP16.
+
+    lattice: None (axis-aligned integer wrap with `origin`) or (R, q) for rotated_cell, the
+    rotation centre being the shape's centre."""
+    if lattice is None:
+        u = tiled_cell(n, cell, origin, z_begin, z_count)
+    else:
+        u = rotated_cell(n, cell, lattice[0], lattice[1], z_begin, z_count, center=center)
     m = mask_values(n, kind, center, size, rot, weights, z_begin, z_count)
     rho = u * m  # float32 * float32 -> float32, one rounding
     if out_dtype == "f16":

@@ -102,3 +102,41 @@ def merge_levels(levels: list[dict], edges: np.ndarray, mode: str = "windows") -
         count[j] = lv["count"][j]
         source[j] = pick
     return {"mean": mean, "sem": sem, "count": count, "mean_q": mean_q, "source": source}
+
+
+def ensemble_sum(items: list[dict], weights) -> dict:
+    """Polydisperse ensemble (Sec. 3: about 200 volume-weighted single-particle simulations
+    combined into one curve), over shared bin edges.
+
+    items: dicts with n (grid edge), count, mean, sem, mean_q (Eq.-1 units of each item);
+    weights: w_i per item (for volume weighting, w_i = phi_i / V_i with phi_i the volume
+    fraction of the size class and V_i the particle volume).
+    Readings: I_ens(Q_j) = sum_i w_i N_i^6 mean_ij (absolute units, electrons^2), valid only
+    where every item of nonzero weight has voxels in bin j (else NaN, count 0);
+    SEM_j = sqrt(sum_i (w_i N_i^6 SEM_ij)^2) (independent items); count and mean |Q| are the
+    sums and the count-weighted mean over the items.
+    """
+    nb = len(items[0]["mean"])
+    mean = np.full(nb, np.nan)
+    sem = np.full(nb, np.nan)
+    count = np.zeros(nb, dtype=np.int64)
+    mean_q = np.full(nb, np.nan)
+    for j in range(nb):
+        ok = all(it["count"][j] > 0 for it, w in zip(items, weights) if w != 0)
+        if not ok:
+            continue
+        s = v = cq = 0.0
+        c = 0
+        for it, w in zip(items, weights):
+            if w == 0:
+                continue
+            sc = float(w) * float(it["n"]) ** 6
+            s += sc * it["mean"][j]
+            v += (sc * it["sem"][j]) ** 2
+            c += int(it["count"][j])
+            cq += it["count"][j] * it["mean_q"][j]
+        mean[j] = s
+        sem[j] = math.sqrt(v)
+        count[j] = c
+        mean_q[j] = cq / c
+    return {"mean": mean, "sem": sem, "count": count, "mean_q": mean_q}

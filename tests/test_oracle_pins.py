@@ -556,3 +556,143 @@ def test_invvar_merge_respects_level_limits_and_falls_back():
     # bin 2 (centre 105): level 1 is beyond its limit
     assert out["source"][2] == 0 and math.isclose(out["mean"][2], 1.0, rel_tol=1e-12)
     assert math.isclose(out["sem"][2], 0.5, rel_tol=1e-12)
+
+
+def test_rotated_lattice_identity_and_quarter_turn_are_exact_index_maps():
+    """Sec. 2.3 rotated sampling of the cell: with R = I and an integer offset the samples
+    fall on cell voxels (weights 0/1) and reproduce the integer wrap exactly; a quarter turn
+    about z permutes the axes exactly."""
+    cell = inputs.mof_like_cell(16, 0.65, 0)
+    n, c = 24, (12.0, 12.0, 12.0)
+    a = density.rotated_cell(n, cell, np.eye(3), (12 + 3, 12 + 5, 12 + 7), center=c)
+    assert np.array_equal(a, density.tiled_cell(n, cell, origin=(3, 5, 7)))
+    quarter = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]], dtype=np.float32)
+    a = density.rotated_cell(n, cell, quarter, c, center=c)
+    zz, yy, xx = np.indices((n, n, n))
+    assert np.array_equal(a, cell[zz % 16, xx % 16, (24 - yy) % 16])
+
+
+def test_rotated_lattice_matches_scipy_grid_wrap_linear_interpolation():
+    """The sampling the paper names (scipy.ndimage.map_coordinates, grid-wrap), at order 1
+    and in float64, agrees with the float32 oracle to float32 rounding."""
+    from scipy import ndimage
+    cell = inputs.mof_like_cell(16, 0.65, 0)
+    n, c = 24, (12.0, 12.0, 12.0)
+    rot = inputs.random_rotation(inputs.SplitMix64(5))
+    q = (12.3, 11.7, 12.9)
+    a = density.rotated_cell(n, cell, rot, q, center=c)
+    zz, yy, xx = np.indices((n, n, n))
+    d = np.stack([xx - 12.0, yy - 12.0, zz - 12.0]).reshape(3, -1)
+    p = rot.astype(np.float64) @ d + np.asarray(q)[:, None]
+    ref = ndimage.map_coordinates(cell.astype(np.float64), [p[2], p[1], p[0]], order=1, mode="grid-wrap")
+    assert np.abs(a - ref.reshape(n, n, n)).max() <= 4e-6 * np.abs(cell).max()
+    # a rotated lattice keeps the cell's mean density to interpolation accuracy
+    big = density.rotated_cell(64, cell, rot, (32.0, 32.0, 32.0), center=(32.0, 32.0, 32.0))
+    assert abs(big.mean() / cell.mean() - 1) < 0.02
+
+
+def test_ensemble_of_voxelised_spheres_follows_the_polydisperse_closed_form():
+    """Sec. 3 polydispersity as volume-weighted single-particle simulations: the ensemble of
+    voxelised uniform spheres of three radii, with w_i = phi_i / V_i and equal volume
+    fractions, follows sum_i w_i (rho V_i)^2 [3 (sin qR_i - qR_i cos qR_i)/(qR_i)^3]^2 at low
+    q, and its forward scattering is rho^2 sum_i phi_i V_i (the volume-weighted mean volume)."""
+    n, dx = 48, 0.1
+    radii = [5.0, 7.0, 9.0]
+    edges = inputs.linear_edges(inputs.nyquist_q(dx), 40)
+    items, vols, nes = [], [], []
+    cell = np.ones((1, 1, 1), dtype=np.float32)
+    for r in radii:
+        sh = inputs.centred_sphere(n, r)
+        rho = density.tile_mask_density(n, cell, density.SPHERE, sh.center, sh.size).astype(np.float64)
+        ob = scatter.forward(rho, dx, edges)
+        items.append({"n": n, "count": ob["count"], "mean": ob["mean"], "sem": ob["sem"], "mean_q": ob["mean_q"]})
+        nes.append(rho.sum())
+        vols.append(rho.sum() * dx ** 3)   # unit density: electrons = voxels
+    phi = [1 / 3] * 3
+    w = [p / v for p, v in zip(phi, vols)]
+    ens = merge.ensemble_sum(items, w)
+    q = ens["mean_q"]
+    th = np.zeros_like(q)
+    for wi, ne, v in zip(w, nes, vols):
+        reff = (3 * v / (4 * math.pi)) ** (1 / 3)
+        th += wi * inputs.sphere_target_curve(q, reff, ne)
+    sel = (ens["count"] > 0) & (q * 9 * dx < 2.0)
+    assert sel.sum() >= 2
+    assert np.all(np.abs(ens["mean"][sel] / th[sel] - 1) < 0.04)
+    # forward scattering through the DC voxel: sum_i w_i N_e,i^2 = sum_i phi_i V_i / dx^6 (unit density)
+    i0 = sum(wi * (float(scatter.dft3(
+        density.tile_mask_density(n, cell, density.SPHERE, inputs.centred_sphere(n, r).center, np.float32(r)))[0, 0, 0].real
+        * n ** 3)) ** 2 for wi, r in zip(w, radii))
+    assert math.isclose(i0, sum(p * v for p, v in zip(phi, vols)) / dx ** 6, rel_tol=1e-12)
+
+
+def test_ensemble_is_linear_and_needs_every_member():
+    nb = 5
+    a = {"n": 8, "count": np.array([3, 3, 0, 3, 3]), "mean": np.array([1.0, 2, 3, 4, 5]) / 8 ** 6,
+         "sem": np.full(nb, 0.1) / 8 ** 6, "mean_q": np.ones(nb)}
+    b = {"n": 16, "count": np.array([4, 4, 4, 4, 0]), "mean": np.array([5.0, 4, 3, 2, 1]) / 16 ** 6,
+         "sem": np.full(nb, 0.2) / 16 ** 6, "mean_q": np.full(nb, 2.0)}
+    e = merge.ensemble_sum([a, b], [2.0, 0.5])
+    assert np.allclose(e["mean"][[0, 1, 3]], 2.0 * np.array([1, 2, 4]) + 0.5 * np.array([5, 4, 2]), rtol=1e-14)
+    assert np.isnan(e["mean"][2]) and np.isnan(e["mean"][4]) and e["count"][2] == 0
+    assert math.isclose(e["sem"][0], math.hypot(2.0 * 0.1, 0.5 * 0.2), rel_tol=1e-14)
+    assert e["count"][0] == 7 and math.isclose(e["mean_q"][0], (3 * 1 + 4 * 2) / 7)
+    # a member of zero weight does not invalidate a bin
+    e = merge.ensemble_sum([a, b], [1.0, 0.0])
+    assert math.isclose(e["mean"][4], 5.0, rel_tol=1e-14) and np.isnan(e["mean"][2])
+
+
+def _ewald_det(**kw):
+    d = {"nx": 33, "ny": 29, "pixel_m": 0.002, "distance_m": 0.5, "beam": (16.0, 14.0), "wavelength_nm": 0.154,
+         "bandwidth": 0.0, "nlambda": 1, "rot": np.eye(3)}
+    d.update(kw)
+    return d
+
+
+def test_ewald_image_of_a_gaussian_follows_its_closed_form():
+    """Sec. 2.5 Ewald-sphere extraction: a well-sampled Gaussian blob has I(q) = I(0)
+    exp(-sigma^2 |q|^2), so each pixel must read that at |q| = (4 pi / lambda) sin(theta),
+    2 theta the pixel's scattering angle; with a wavelength band, the mean over the band."""
+    from oracle import ewald
+    n, dx, sv = 64, 0.05, 1.0
+    zz, yy, xx = np.indices((n, n, n)).astype(np.float64)
+    rho = np.exp(-((xx - 32) ** 2 + (yy - 32) ** 2 + (zz - 32) ** 2) / (2 * sv * sv))
+    F = scatter.dft3(rho)
+    i0 = scatter.intensity(F)[0, 0, 0]
+    sig = sv * dx
+    for det in (_ewald_det(pixel_m=0.006),
+                _ewald_det(pixel_m=0.006, bandwidth=0.1, nlambda=5, rot=inputs.random_rotation(inputs.SplitMix64(2)))):
+        img = ewald.ewald_image(F, dx, det)
+        s = ewald.pixel_directions(det)
+        two_theta = np.arccos(np.clip(s[..., 2], -1, 1))
+        want = np.zeros_like(img)
+        for lam in ewald.wavelengths(det):
+            q = 4 * math.pi / lam * np.sin(two_theta / 2)
+            want += i0 * np.exp(-(sig * q) ** 2)
+        want /= len(ewald.wavelengths(det))
+        ok = np.isfinite(img) & (want > 1e-3 * i0)
+        assert ok.sum() > 100
+        # trilinear interpolation of a Gaussian 10 grid steps wide: under 1 %
+        assert np.max(np.abs(img[ok] / want[ok] - 1)) < 0.01
+
+
+def test_ewald_beam_centre_reads_forward_scattering_and_trilinear_is_scipys():
+    """The direct-beam pixel samples q = 0 (I(0) exactly, at every wavelength); the
+    interpolation agrees with scipy.ndimage.map_coordinates at order 1."""
+    from scipy import ndimage
+    from oracle import ewald
+    n, dx = 16, 0.2
+    rho = RNG.random((n, n, n))
+    F = scatter.dft3(rho)
+    I = scatter.intensity(F)
+    det = _ewald_det(nx=9, ny=9, beam=(4.0, 4.0), pixel_m=0.02, distance_m=0.3, wavelength_nm=0.5,
+                     bandwidth=0.2, nlambda=3, rot=inputs.random_rotation(inputs.SplitMix64(8)))
+    img = ewald.ewald_image(F, dx, det)
+    assert img[4, 4] == I[0, 0, 0]
+    kf = ewald.q_samples(det) / scatter.dq_of(n, dx)
+    val, valid = ewald.trilinear(I, kf)
+    Ish = np.fft.fftshift(I)
+    ref = ndimage.map_coordinates(Ish, [kf[..., 2].ravel() + n // 2, kf[..., 1].ravel() + n // 2,
+                                        kf[..., 0].ravel() + n // 2], order=1, mode="nearest").reshape(val.shape)
+    assert valid.sum() > 50
+    assert np.allclose(val[valid], ref[valid], rtol=1e-12, atol=1e-15)
