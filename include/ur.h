@@ -111,12 +111,15 @@ ur_status ur_bin_thresholds(int32_t n, double dx, const double* edges, int32_t n
  * ur_fault_reset() re-reads the variable.  Nothing on the device is faulted. */
 void ur_fault_reset(void);
 
-enum { UR_WS_FORWARD = 1, UR_WS_BACKWARD = 2, UR_WS_HOST_SLABS = 4 };
+enum { UR_WS_FORWARD = 1, UR_WS_BACKWARD = 2, UR_WS_HOST_SLABS = 4, UR_WS_ADJ_SLABS = 8 };
 /* Workspace bytes for the operations in `what` (bitwise OR of UR_WS_*).
  * The forward workspace holds the plane-transform intermediate
  * (nz * N * (N/2+1) complex64) and the per-block bin partials; the backward
  * adds the inverse intermediate (N * N * (N/2+1) complex64).  UR_WS_HOST_SLABS
- * adds two staging slabs for ED read from pinned host memory. */
+ * adds two staging slabs for ED read from pinned host memory.  UR_WS_ADJ_SLABS
+ * (ur_backward_slabs) adds, after the forward part and the host staging slabs
+ * (counted whether or not UR_WS_HOST_SLABS is given), one slab of the inverse
+ * intermediate and two dL/dm staging slabs of ur_plan_set_adj_slab_planes planes. */
 size_t ur_workspace_size(const ur_plan* plan, int32_t what);
 
 /* Planes per host->device slab of the out-of-core path (default: about
@@ -134,6 +137,20 @@ ur_status ur_plan_set_slab_planes(ur_plan* plan, int32_t planes);
  * which does not chunk). */
 ur_status ur_plan_set_chunk_planes(ur_plan* plan, int32_t planes);
 int32_t ur_plan_chunk_planes(const ur_plan* plan);
+
+/* Voxel-sinc correction of the binned intensity (Sec. 2.5 last paragraph: the
+ * pattern taken with the voxel-sized sinc for better high-Q behaviour, left out
+ * by the paper for its tiny voxels).  Reading: the voxelised density is a sum
+ * of uniform cubes of edge dx, whose form factor multiplies the transform, so
+ * with the option on every binned intensity is |F_k|^2 times
+ * S(k) = prod_a sinc^2(pi k_a / N) (sinc x = sin x / x).  It brings the zoom
+ * levels of ur_merge into agreement below each coarse level's limit (for a
+ * density that is constant on the coarse voxels, exactly).  The plan keeps a
+ * table of sinc^2(pi m / N) (float64-built, stored float32).  Counts and sum |Q|
+ * are unchanged.  The adjoint (ur_backward, batches with an adjoint) rejects
+ * such plans with UR_ERR_UNSUPPORTED.  ur_plan_voxel_sinc returns 1 when on. */
+ur_status ur_plan_set_voxel_sinc(ur_plan* plan, int32_t on);
+int32_t ur_plan_voxel_sinc(const ur_plan* plan);
 
 /* ---------------------------------------------------------------------------
  * ur_build_density (Sec. 2.3).
@@ -161,6 +178,29 @@ ur_status ur_build_density(int32_t n, const float* cell, int32_t ucell, const in
                            const ur_shape* shape, const float* weights, int32_t z_begin,
                            int32_t z_count, int32_t out_dtype, void* ed_out, int32_t* nz_range,
                            void* stream);
+
+/* Rotated lattice (Sec. 2.3 first paragraph: the cell interpolated over rotated
+ * planes with the cell repeated outside its bounds, the route to crystallites
+ * of any orientation).  Voxel (x, y, z) samples the cell at the cell-voxel
+ * coordinate p = R (x - c) + q, c = the shape's centre, by trilinear
+ * interpolation of the periodic cell (order 1).  Every product, sum and
+ * difference is rounded separately in float32, in the order
+ * p_a = ((R[a][0] d_0 + R[a][1] d_1) + R[a][2] d_2) + q_a with d = (x, y, z) - c;
+ * i = floor(p), f = p - i; lerp(a, b, f) = a + f (b - a) along x, then y, then z
+ * over the neighbours (i + {0, 1}) mod U.  With R = I and an integer q the
+ * samples are cell voxels: the integer wrap of ur_build_density with origin
+ * q - c. */
+typedef struct {
+  float rot[9];     /* row-major R */
+  float offset[3];  /* q, cell-voxel units */
+} ur_lattice;
+
+/* ur_build_density with the cell sampled on a rotated lattice (lattice
+ * non-NULL; all other arguments as for ur_build_density, without an origin).
+ * The adjoint (ur_backward) does not take a lattice. */
+ur_status ur_build_density_lattice(int32_t n, const float* cell, int32_t ucell, const ur_lattice* lattice,
+                                   const ur_shape* shape, const float* weights, int32_t z_begin, int32_t z_count,
+                                   int32_t out_dtype, void* ed_out, int32_t* nz_range, void* stream);
 
 /* ED-2/ED-3 (Sec. 2.3): out[Z][Y][X] = sum of src over the f^3 block at
  * (f Z', f Y', f X') where (Z', Y', X') = (Z, Y, X) - o, o = (n_out - n_src/f)/2,
@@ -196,6 +236,12 @@ ur_status ur_fft_intensity(const ur_plan* plan, const void* ed, int32_t ed_on_ho
 ur_status ur_fft_intensity_tiled(const ur_plan* plan, const float* cell, int32_t ucell, const int32_t* origin,
                                  const ur_shape* shape, const float* weights, double* bins, void* F_out, void* ws,
                                  size_t ws_bytes, void* stream);
+
+/* ur_fft_intensity_tiled with the density of ur_build_density_lattice (the cell
+ * sampled on a rotated lattice) generated inside the plane pass. */
+ur_status ur_fft_intensity_tiled_lattice(const ur_plan* plan, const float* cell, int32_t ucell,
+                                         const ur_lattice* lattice, const ur_shape* shape, const float* weights,
+                                         double* bins, void* F_out, void* ws, size_t ws_bytes, void* stream);
 
 /* ur_fft_intensity_noalloc -- the paper has no counterpart; this entry point
  * serves callers that must not allocate device memory while they run (a
@@ -268,6 +314,63 @@ ur_status ur_merge(int32_t nlev, const double* const* level_bins, const int32_t*
 double ur_level_qmax(double dx);
 
 /* ---------------------------------------------------------------------------
+ * Ewald-sphere detector image (Sec. 2.5 first paragraph: for anisotropic
+ * samples, the 2D data of a practical experiment are the intensity read on the
+ * Ewald sphere, a shell whose thickness the wavelength distribution sets).
+ *   F_half  device complex64 [N][N][N/2+1], the F_out of ur_fft_intensity
+ *           (Eq. 1 normalised)
+ *   det     host; a flat detector normal to the beam (+z) at distance_m;
+ *           pixel (ix, iy) at ((ix - beam_x) pixel_m, (iy - beam_y) pixel_m);
+ *           nlambda wavelengths lambda_l = wavelength_nm (1 + bandwidth ((l +
+ *           1/2)/nlambda - 1/2)) (uniform band of relative full width
+ *           `bandwidth`, 1 <= nlambda <= 16); rot = sample orientation R
+ *           (row-major), q_sample = R^T q_lab.
+ *   image   device float32 [ny][nx]: per pixel the mean over wavelengths of
+ *           |F|^2 at q = (2 pi / lambda)(s - z_hat) (s the unit vector to the
+ *           pixel), trilinearly interpolated between the 8 neighbouring grid
+ *           frequencies (F(-k) = conj F(k) for the missing half); samples whose
+ *           neighbours leave [-N/2, N/2 - 1] are dropped; NaN where none is left.
+ *           Eq. 1 units (times N^6 for electrons^2).  Geometry in float32.
+ * Errors: UR_ERR_INVALID for null pointers, sizes outside range or a
+ * non-positive pixel, distance or wavelength.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t nx, ny;
+  double pixel_m, distance_m;
+  double beam_x, beam_y;
+  double wavelength_nm, bandwidth;
+  int32_t nlambda;
+  float rot[9];
+} ur_detector;
+ur_status ur_ewald_image(const ur_plan* plan, const void* F_half, const ur_detector* det, float* image, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Polydisperse ensemble (Sec. 3: broad polydispersity described by about 200
+ * volume-weighted single-particle simulations, summed into one curve).
+ *   count        number of particles (1..512)
+ *   item_bins    host array of device pointers, each double[UR_BIN_FIELDS][B]
+ *                over the same edges (e.g. the bins of a ur_batch)
+ *   item_n       host int32[count], grid edge of each particle (scale N^6)
+ *   weights      host double[count], w_i; volume weighting is w_i = phi_i / V_i
+ *                (phi_i the volume fraction of the size class, V_i the volume)
+ *   out          device double[4][B]: mean = sum_i w_i N_i^6 mean_ij (absolute
+ *                units), SEM = sqrt(sum_i (w_i N_i^6 SEM_ij)^2), count, mean |Q|.
+ *                A bin is NaN (count 0) unless every particle of nonzero
+ *                weight has voxels in it.
+ * ur_ensemble_backward scatters dL/d(ensemble mean) to each particle:
+ * item_dl_dmean[i][j] = w_i N_i^6 dl_dens[j] on valid bins, 0 elsewhere (host
+ * array of device pointers, each double[B], ready for ur_backward or a batch).
+ * One kernel launch each; the tables are kernel parameters (capturable).
+ * Errors: UR_ERR_INVALID for a count outside [1, 512], null pointers, N <= 0
+ * or a weight that is not finite.
+ * ------------------------------------------------------------------------- */
+ur_status ur_ensemble(int32_t count, const double* const* item_bins, const int32_t* item_n, const double* weights,
+                      int32_t nbins, double* out, void* stream);
+ur_status ur_ensemble_backward(int32_t count, const double* const* item_bins, const int32_t* item_n,
+                               const double* weights, int32_t nbins, const double* dl_dens,
+                               double* const* item_dl_dmean, void* stream);
+
+/* ---------------------------------------------------------------------------
  * ur_backward: adjoint of ur_build_density + ur_fft_intensity for a loss L
  * on the bin means (not in the paper).
  *   dl_dmean  device double[B], dL/d(mean I_j)
@@ -288,6 +391,26 @@ ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double*
                       const float* weights, float* dl_dcell, float* dl_dmask, void* ws, size_t ws_bytes,
                       void* stream);
 
+/* Out-of-core adjoint (the per-slab adjoint of config-sized grids whose inverse
+ * intermediate of all N planes, N * N * (N/2+1) complex64, does not fit; the
+ * paper's Sec. 2.4 slice-wise processing applied to the adjoint).  Same
+ * result as ur_backward with F = NULL, computed slab by slab: for each slab of
+ * adj_slab_planes output planes the z pass is recomputed over every spectrum
+ * column from the forward intermediate in ws (recomputation instead of storing
+ * F), and only the slab's planes go through the y inverse and the row pass.
+ * dL/du accumulates on the device; dL/dm (optional) is written slab by slab to
+ * dl_dmask_host, pinned host float32 [N][N][N], by a copy stream overlapping the
+ * next slab (two device staging slabs).  ws: the forward's workspace, sized
+ * with UR_WS_FORWARD | UR_WS_ADJ_SLABS, still holding the forward intermediate.
+ * Power-of-two grids only (UR_ERR_INVALID otherwise); plans with the voxel-sinc
+ * correction get UR_ERR_UNSUPPORTED.  The caller's stream waits for the copies. */
+ur_status ur_backward_slabs(const ur_plan* plan, const double* dl_dmean, const double* fwd_bins, const float* cell,
+                            int32_t ucell, const int32_t* origin, const ur_shape* shape, const float* weights,
+                            float* dl_dcell, float* dl_dmask_host, void* ws, size_t ws_bytes, void* stream);
+/* Output planes per slab of ur_backward_slabs (default: about 4 GiB of inverse
+ * intermediate); changes ur_workspace_size(plan, UR_WS_ADJ_SLABS). */
+ur_status ur_plan_set_adj_slab_planes(ur_plan* plan, int32_t planes);
+
 /* Log-I(Q) mean-squared error against a target curve and its gradient, the
  * loss of the batched workload and of the benchmark step (not in the paper;
  * the fit of a simulated curve to a measured one that Sec. 3 motivates):
@@ -297,7 +420,9 @@ ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double*
  * bins: device double[UR_BIN_FIELDS][nbins] from a forward; target: device
  * double[nbins] (positive where bins are valid); loss: device double[1] or NULL;
  * dl_dmean: device double[nbins] (overwritten), ready for ur_backward.  One
- * kernel launch, float64 throughout; nbins <= 8192 (UR_ERR_INVALID above). */
+ * kernel launch (plus a memset of *loss), float64 throughout; L is summed over
+ * blocks with atomics, so its last bits may depend on scheduling; nbins <= 8192
+ * (UR_ERR_INVALID above). */
 ur_status ur_log_mse_grad(int32_t nbins, const double* bins, const double* target, double* loss, double* dl_dmean,
                           void* stream);
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libur.so")
 
 UR_F32, UR_F16 = 0, 1
-UR_WS_FORWARD, UR_WS_BACKWARD, UR_WS_HOST_SLABS = 1, 2, 4
+UR_WS_FORWARD, UR_WS_BACKWARD, UR_WS_HOST_SLABS, UR_WS_ADJ_SLABS = 1, 2, 4, 8
 BIN_FIELDS = 6
 BIN_COUNT, BIN_SUM_I, BIN_SUM_I2, BIN_SUM_Q, BIN_MEAN, BIN_SEM = range(6)
 STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID", 2: "UR_ERR_OOM", 3: "UR_ERR_CUDA", 4: "UR_ERR_TIMEOUT",
@@ -32,6 +32,29 @@ class GridDesc(C.Structure):
 
 class ShapeDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("center", C.c_float * 3), ("size", C.c_float), ("rot", C.c_float * 9)]
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("rot", C.c_float * 9), ("offset", C.c_float * 3)]
+
+
+def lattice_desc(lattice) -> LatticeDesc:
+    """(R, q) -> ur_lattice: sample point p = R (x - c) + q in cell-voxel units."""
+    rot, off = lattice
+    d = LatticeDesc()
+    r = np.asarray(rot, dtype=np.float32).reshape(9)
+    for i in range(9):
+        d.rot[i] = float(r[i])
+    o = np.asarray(off, dtype=np.float32)
+    for i in range(3):
+        d.offset[i] = float(o[i])
+    return d
+
+
+class DetectorDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("pixel_m", C.c_double), ("distance_m", C.c_double),
+                ("beam_x", C.c_double), ("beam_y", C.c_double), ("wavelength_nm", C.c_double),
+                ("bandwidth", C.c_double), ("nlambda", C.c_int32), ("rot", C.c_float * 9)]
 
 
 class BatchItem(C.Structure):
@@ -53,17 +76,27 @@ SIGNATURES = {
     "ur_plan_set_slab_planes": (_i32, [_vp, _i32]),
     "ur_build_density": (_i32, [_i32, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _i32, _i32, _i32,
                                 _vp, _vp, _vp]),
+    "ur_build_density_lattice": (_i32, [_i32, _vp, _i32, C.POINTER(LatticeDesc), C.POINTER(ShapeDesc), _vp, _i32, _i32,
+                                        _i32, _vp, _vp, _vp]),
     "ur_zoom_density": (_i32, [_i32, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),
     "ur_fft_intensity": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
     "ur_fft_intensity_tiled": (_i32, [_vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp, _vp,
                                       _sz, _vp]),
+    "ur_fft_intensity_tiled_lattice": (_i32, [_vp, _vp, _i32, C.POINTER(LatticeDesc), C.POINTER(ShapeDesc), _vp, _vp,
+                                              _vp, _vp, _sz, _vp]),
     "ur_fft_intensity_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "ur_noalloc_scratch_bytes": (_sz, []),
     "ur_bin_q": (_i32, [_vp, _vp, _vp, _vp, _sz, _vp]),
     "ur_merge": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _vp, _i32, _i32, _vp, _vp]),
     "ur_level_qmax": (C.c_double, [C.c_double]),
+    "ur_ewald_image": (_i32, [_vp, _vp, C.POINTER(DetectorDesc), _vp, _vp]),
+    "ur_ensemble": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _i32, _vp, _vp]),
+    "ur_ensemble_backward": (_i32, [_i32, C.POINTER(_vp), C.POINTER(C.c_int32), _dp, _i32, _vp, C.POINTER(_vp), _vp]),
     "ur_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
                            _vp, _sz, _vp]),
+    "ur_backward_slabs": (_i32, [_vp, _vp, _vp, _vp, _i32, C.POINTER(C.c_int32), C.POINTER(ShapeDesc), _vp, _vp, _vp,
+                                 _vp, _sz, _vp]),
+    "ur_plan_set_adj_slab_planes": (_i32, [_vp, _i32]),
     "ur_set_timing": (None, [_i32]),
     "ur_last_timings": (_i32, [C.POINTER(C.c_float), _i32, C.POINTER(C.c_char_p)]),
     "ur_batch_create": (_i32, [_i32, _vp, C.POINTER(_vp)]),
@@ -76,11 +109,14 @@ SIGNATURES = {
     "ur_log_mse_grad": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "ur_plan_chunk_planes": (_i32, [_vp]),
     "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ur_plan_set_voxel_sinc": (_i32, [_vp, _i32]),
+    "ur_plan_voxel_sinc": (_i32, [_vp]),
 }
 # test hooks (not part of the header's API)
 EXTRA = {
     "ur_selftest_fastdiv": (C.c_int64, []),
     "ur_selftest_dft": (C.c_double, []),
+    "ur_selftest_wait_timeout": (_i32, [_vp]),
 }
 
 _lib = None
@@ -188,8 +224,18 @@ class Plan:
     def set_slab_planes(self, planes: int):
         _check("ur_plan_set_slab_planes", lib().ur_plan_set_slab_planes(self._h, int(planes)))
 
+    def set_adj_slab_planes(self, planes: int):
+        _check("ur_plan_set_adj_slab_planes", lib().ur_plan_set_adj_slab_planes(self._h, int(planes)))
+
     def set_chunk_planes(self, planes: int):
         _check("ur_plan_set_chunk_planes", lib().ur_plan_set_chunk_planes(self._h, int(planes)))
+
+    def set_voxel_sinc(self, on: bool = True):
+        """Bin |F|^2 times the voxel form factor prod_a sinc^2(pi k_a / N) (Sec. 2.5 sinc correction)."""
+        _check("ur_plan_set_voxel_sinc", lib().ur_plan_set_voxel_sinc(self._h, 1 if on else 0))
+
+    def voxel_sinc(self) -> bool:
+        return bool(lib().ur_plan_voxel_sinc(self._h))
 
     def chunk_planes(self) -> int:
         return int(lib().ur_plan_chunk_planes(self._h))
@@ -226,15 +272,22 @@ class Plan:
 
 def build_density(n: int, cell: torch.Tensor, shape, origin=(0, 0, 0), weights: torch.Tensor | None = None,
                   z_begin: int = 0, z_count: int | None = None, out_dtype="f32", out: torch.Tensor | None = None,
-                  nz_range: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """ED-1 planes [z_begin, z_begin + z_count) (Sec. 2.3 tile + mask)."""
+                  nz_range: torch.Tensor | None = None, lattice=None, stream=None) -> torch.Tensor:
+    """ED-1 planes [z_begin, z_begin + z_count) (Sec. 2.3 tile + mask); lattice = (R, q) samples the
+    cell on a rotated lattice instead of the integer wrap with `origin`."""
     z_count = n - z_begin if z_count is None else z_count
     code = _dtype_code(out_dtype)
     if out is None:
         out = torch.empty((z_count, n, n), dtype=_torch_dtype(code), device=cell.device)
     assert cell.is_cuda and cell.dtype == torch.float32 and cell.is_contiguous()
-    org = (C.c_int32 * 3)(*[int(v) for v in origin])
     sd = shape_desc(shape)
+    if lattice is not None:
+        ld = lattice_desc(lattice)
+        _check("ur_build_density_lattice", lib().ur_build_density_lattice(
+            n, _ptr(cell), cell.shape[0], C.byref(ld), C.byref(sd), _ptr(weights), z_begin, z_count, code, _ptr(out),
+            _ptr(nz_range), _stream(stream)))
+        return out
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
     _check("ur_build_density", lib().ur_build_density(n, _ptr(cell), cell.shape[0], org, C.byref(sd), _ptr(weights),
                                                       z_begin, z_count, code, _ptr(out), _ptr(nz_range), _stream(stream)))
     return out
@@ -274,14 +327,20 @@ def fft_intensity(plan: Plan, ed: torch.Tensor, bins: torch.Tensor | None = None
 
 def fft_intensity_tiled(plan: Plan, cell: torch.Tensor, shape, origin=(0, 0, 0), weights: torch.Tensor | None = None,
                         bins: torch.Tensor | None = None, F_out: torch.Tensor | None = None,
-                        ws: torch.Tensor | None = None, stream=None, want_bins: bool = True):
+                        ws: torch.Tensor | None = None, stream=None, want_bins: bool = True, lattice=None):
     """Sec. 2.3 + 2.4 + 2.5 fused: density generated inside the plane pass, never stored."""
     if ws is None:
         ws = plan.workspace(UR_WS_FORWARD)
     if bins is None and want_bins:
         bins = new_bins(plan)
-    org = (C.c_int32 * 3)(*[int(v) for v in origin])
     sd = shape_desc(shape)
+    if lattice is not None:
+        ld = lattice_desc(lattice)
+        _check("ur_fft_intensity_tiled_lattice", lib().ur_fft_intensity_tiled_lattice(
+            plan.handle, _ptr(cell), cell.shape[0], C.byref(ld), C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
+            _ptr(ws), ws.numel(), _stream(stream)))
+        return bins
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
     _check("ur_fft_intensity_tiled", lib().ur_fft_intensity_tiled(plan.handle, _ptr(cell), cell.shape[0], org,
                                                                   C.byref(sd), _ptr(weights), _ptr(bins), _ptr(F_out),
                                                                   _ptr(ws), ws.numel(), _stream(stream)))
@@ -346,6 +405,52 @@ def merge(level_bins: list, level_n: list, level_dx: list, edges_dev: torch.Tens
     return out
 
 
+def ensemble(item_bins: list, item_n: list, weights, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Sec. 3 polydisperse ensemble: out[4, B] = mean (sum_i w_i N_i^6 mean_i), SEM, count, mean Q."""
+    k = len(item_bins)
+    nb = item_bins[0].shape[1]
+    if out is None:
+        out = torch.empty((4, nb), dtype=torch.float64, device=item_bins[0].device)
+    ptrs = (C.c_void_p * k)(*[b.data_ptr() for b in item_bins])
+    ns = (C.c_int32 * k)(*[int(v) for v in item_n])
+    ws = np.ascontiguousarray(weights, dtype=np.float64)
+    _check("ur_ensemble", lib().ur_ensemble(k, ptrs, ns, ws.ctypes.data_as(_dp), nb, _ptr(out), _stream(stream)))
+    return out
+
+
+def ensemble_backward(item_bins: list, item_n: list, weights, dl_dens: torch.Tensor, item_dl_dmean: list,
+                      stream=None):
+    """dL/d(each particle's bin means) from dL/d(ensemble mean) (written into item_dl_dmean)."""
+    k = len(item_bins)
+    nb = item_bins[0].shape[1]
+    ptrs = (C.c_void_p * k)(*[b.data_ptr() for b in item_bins])
+    gp = (C.c_void_p * k)(*[g.data_ptr() for g in item_dl_dmean])
+    ns = (C.c_int32 * k)(*[int(v) for v in item_n])
+    ws = np.ascontiguousarray(weights, dtype=np.float64)
+    _check("ur_ensemble_backward", lib().ur_ensemble_backward(k, ptrs, ns, ws.ctypes.data_as(_dp), nb, _ptr(dl_dens),
+                                                              gp, _stream(stream)))
+    return item_dl_dmean
+
+
+def ewald_image(plan: Plan, F_half: torch.Tensor, det: dict, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Sec. 2.5 detector image on the Ewald sphere from the half spectrum F (F_out of a forward).
+    det: nx, ny, pixel_m, distance_m, beam (bx, by), wavelength_nm, bandwidth, nlambda, rot."""
+    d = DetectorDesc()
+    d.nx, d.ny = int(det["nx"]), int(det["ny"])
+    d.pixel_m, d.distance_m = float(det["pixel_m"]), float(det["distance_m"])
+    d.beam_x, d.beam_y = float(det["beam"][0]), float(det["beam"][1])
+    d.wavelength_nm, d.bandwidth = float(det["wavelength_nm"]), float(det.get("bandwidth", 0.0))
+    d.nlambda = int(det.get("nlambda", 1))
+    r = np.asarray(det.get("rot", np.eye(3)), dtype=np.float32).reshape(9)
+    for i in range(9):
+        d.rot[i] = float(r[i])
+    if out is None:
+        out = torch.empty((d.ny, d.nx), dtype=torch.float32, device=F_half.device)
+    _check("ur_ewald_image", lib().ur_ewald_image(plan.handle, _ptr(F_half), C.byref(d), _ptr(out), _stream(stream)))
+    return out
+
+
 def level_qmax(dx: float) -> float:
     """The |Q| up to which ur_merge trusts a level of voxel edge dx (computed by the library)."""
     return float(lib().ur_level_qmax(float(dx)))
@@ -368,6 +473,23 @@ def backward(plan: Plan, dl_dmean: torch.Tensor, fwd_bins: torch.Tensor, cell: t
                                             cell.shape[0], org, C.byref(sd), _ptr(weights), _ptr(dl_dcell),
                                             _ptr(dl_dmask), _ptr(ws), ws.numel(), _stream(stream)))
     return dl_dcell, dl_dmask
+
+
+def backward_slabs(plan: Plan, dl_dmean: torch.Tensor, fwd_bins: torch.Tensor, cell: torch.Tensor, shape,
+                   ws: torch.Tensor, origin=(0, 0, 0), weights: torch.Tensor | None = None,
+                   dl_dcell: torch.Tensor | None = None, dl_dmask_host: torch.Tensor | None = None, stream=None):
+    """Out-of-core adjoint: dL/d cell on the device, dL/d mask (optional) into pinned host memory,
+    slab by slab with the z pass recomputed per slab.  `ws` (UR_WS_FORWARD | UR_WS_ADJ_SLABS) still
+    holds the forward intermediate."""
+    if dl_dcell is None:
+        dl_dcell = torch.empty_like(cell)
+    org = (C.c_int32 * 3)(*[int(v) for v in origin])
+    sd = shape_desc(shape)
+    _check("ur_backward_slabs", lib().ur_backward_slabs(plan.handle, _ptr(dl_dmean), _ptr(fwd_bins), _ptr(cell),
+                                                        cell.shape[0], org, C.byref(sd), _ptr(weights),
+                                                        _ptr(dl_dcell), _ptr(dl_dmask_host), _ptr(ws), ws.numel(),
+                                                        _stream(stream)))
+    return dl_dcell, dl_dmask_host
 
 
 def bin_thresholds(n: int, dx: float, edges) -> np.ndarray:

@@ -141,65 +141,64 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
 
 __global__ void __launch_bounds__(256, 2) k_rows_grad(GenGradArgs g) { rows_grad_body(g, blockIdx.x, blockIdx.y); }
 
-// Log-I(Q) MSE and its gradient in one block of 1024 threads: each thread keeps
-// the log differences of its (at most 8) bins in registers, the number of valid
-// bins and the sum of squares are block-reduced, then every bin's gradient is
-// written.  float64 throughout.
-#define UR_LOSS_THREADS 1024
-#define UR_LOSS_PER_THREAD 8
+// Log-I(Q) MSE and its gradient: one thread per bin over blocks of 64 threads
+// (the float64 logarithms are the cost, so they are spread over many SMs).
+// Every block first counts the valid bins of the whole curve (V, needed by the
+// gradient of every bin; a cheap scan), then writes its bins' gradients and
+// adds its share of L = sum d^2 / V to *loss (zeroed beforehand).  float64
+// throughout.
+#define UR_LOSS_THREADS 64
+#define UR_LOSS_MAX_BINS 8192
 __global__ void __launch_bounds__(UR_LOSS_THREADS) k_log_mse_grad(int nb, const double* __restrict__ bins,
                                                                   const double* __restrict__ target,
                                                                   double* __restrict__ loss, double* __restrict__ g) {
-  __shared__ double s_sum[UR_LOSS_THREADS / 32];
   __shared__ int s_cnt[UR_LOSS_THREADS / 32];
+  __shared__ double s_sum[UR_LOSS_THREADS / 32];
   const double* mean = bins + (size_t)UR_BIN_MEAN * nb;
-  double d[UR_LOSS_PER_THREAD], m[UR_LOSS_PER_THREAD];
-  double ss = 0.0;
   int cnt = 0;
-#pragma unroll
-  for (int u = 0; u < UR_LOSS_PER_THREAD; ++u) {
-    const int j = threadIdx.x + u * UR_LOSS_THREADS;
-    m[u] = j < nb ? mean[j] : 0.0;
-    d[u] = 0.0;
-    if (j < nb && isfinite(m[u]) && m[u] > 0.0) {
-      d[u] = log(m[u]) - log(target[j]);
-      ss += d[u] * d[u];
-      ++cnt;
-    }
+  for (int j = threadIdx.x; j < nb; j += UR_LOSS_THREADS) {
+    const double m = mean[j];
+    cnt += (isfinite(m) && m > 0.0) ? 1 : 0;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ss += __shfl_down_sync(0xffffffffu, ss, o);
-    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_sum[threadIdx.x >> 5] = ss;
-    s_cnt[threadIdx.x >> 5] = cnt;
-  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
   __syncthreads();
-  double tot = 0.0;
   int ntot = 0;
-  for (int w = 0; w < UR_LOSS_THREADS / 32; ++w) {  // the same order on every thread
-    tot += s_sum[w];
-    ntot += s_cnt[w];
-  }
+  for (int w = 0; w < UR_LOSS_THREADS / 32; ++w) ntot += s_cnt[w];
   const double nv = (double)(ntot > 0 ? ntot : 1);
-  if (threadIdx.x == 0 && loss) *loss = tot / nv;
+  const int j = blockIdx.x * UR_LOSS_THREADS + threadIdx.x;
+  double d2 = 0.0;
+  if (j < nb) {
+    const double m = mean[j];
+    double gj = 0.0;
+    if (isfinite(m) && m > 0.0) {
+      const double d = log(m) - log(target[j]);
+      d2 = d * d;
+      gj = 2.0 * d / (m * nv);
+    }
+    g[j] = gj;
+  }
 #pragma unroll
-  for (int u = 0; u < UR_LOSS_PER_THREAD; ++u) {
-    const int j = threadIdx.x + u * UR_LOSS_THREADS;
-    if (j < nb) g[j] = (isfinite(m[u]) && m[u] > 0.0) ? 2.0 * d[u] / (m[u] * nv) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) d2 += __shfl_down_sync(0xffffffffu, d2, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = d2;
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) {
+    double tot = 0.0;
+    for (int w = 0; w < UR_LOSS_THREADS / 32; ++w) tot += s_sum[w];
+    if (tot != 0.0) atomicAdd(loss, tot / nv);
   }
 }
 
 extern "C" ur_status ur_log_mse_grad(int32_t nbins, const double* bins, const double* target, double* loss,
                                      double* dl_dmean, void* stream) {
   UR_REQUIRE(nbins >= 1 && bins && target && dl_dmean, "ur_log_mse_grad: bad argument");
-  UR_REQUIRE(nbins <= UR_LOSS_THREADS * UR_LOSS_PER_THREAD, "ur_log_mse_grad: %d bins (at most %d)", nbins,
-             UR_LOSS_THREADS * UR_LOSS_PER_THREAD);
+  UR_REQUIRE(nbins <= UR_LOSS_MAX_BINS, "ur_log_mse_grad: %d bins (at most %d)", nbins, UR_LOSS_MAX_BINS);
   cudaStream_t s = (cudaStream_t)stream;
   ur_timing_begin("loss_grad", s);
-  k_log_mse_grad<<<1, UR_LOSS_THREADS, 0, s>>>(nbins, bins, target, loss, dl_dmean);
+  if (loss) UR_CUDA_CHECK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+  k_log_mse_grad<<<(nbins + UR_LOSS_THREADS - 1) / UR_LOSS_THREADS, UR_LOSS_THREADS, 0, s>>>(nbins, bins, target, loss,
+                                                                                              dl_dmean);
   UR_LAUNCH_CHECK("k_log_mse_grad");
   ur_timing_end(s);
   return UR_OK;
@@ -217,6 +216,10 @@ extern "C" ur_status ur_backward(const ur_plan* p, const double* dl_dmean, const
   UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_backward: bad shape kind");
   UR_REQUIRE(shape->kind != UR_SHAPE_WEIGHTS || weights, "ur_backward: weights required for UR_SHAPE_WEIGHTS");
   UR_REQUIRE(!dl_dmask || ((uintptr_t)dl_dmask % 8) == 0, "ur_backward: dl_dmask must be 8-byte aligned");
+  if (p->vsinc) {
+    ur_set_error("ur_backward: the adjoint of the voxel-sinc corrected binning is not built");
+    return UR_ERR_UNSUPPORTED;
+  }
   UR_TRY(ur_fault_point("backward"));
   cudaStream_t s = (cudaStream_t)stream;
   const int n = p->n, H = p->H, nb = p->nbins;
@@ -413,4 +416,174 @@ ur_status ur_batch_launch_grad(const BatchGradItem* items, const long long* star
   k_batch_grad<<<(unsigned)nblocks, 256, smem, s>>>(items, start, count);
   UR_LAUNCH_CHECK("k_batch_grad");
   return UR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Out-of-core adjoint (the per-slab adjoint of the streamed forward): the inverse
+// intermediate of all N planes does not fit when the grid is large, so the output planes
+// are produced slab by slab.  For every slab the z pass is recomputed over all spectrum
+// columns from the forward intermediate (F~ along z, times sigma(bin), inverse along z)
+// and only the slab's planes are kept; the slab then goes through the y inverse and the
+// row pass (dL/du accumulated, dL/dm written to a device staging buffer and copied to
+// pinned host memory on a copy stream, double-buffered).
+// ---------------------------------------------------------------------------
+extern "C" ur_status ur_plan_set_adj_slab_planes(ur_plan* p, int32_t planes) {
+  UR_REQUIRE(p && planes >= 1, "ur_plan_set_adj_slab_planes: bad argument");
+  p->adj_slab_planes = planes > p->n ? p->n : planes;
+  return UR_OK;
+}
+
+extern "C" ur_status ur_backward_slabs(const ur_plan* p, const double* dl_dmean, const double* fwd_bins,
+                                       const float* cell, int32_t ucell, const int32_t* origin, const ur_shape* shape,
+                                       const float* weights, float* dl_dcell, float* dl_dmask_host, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  UR_REQUIRE(p && dl_dmean && fwd_bins && cell && shape && dl_dcell && ws, "ur_backward_slabs: null argument");
+  UR_REQUIRE(p->fast, "ur_backward_slabs: power-of-two grids only (edge %d)", p->n);
+  UR_REQUIRE(ucell >= 1, "ur_backward_slabs: empty cell");
+  UR_REQUIRE(!origin || (origin[0] >= 0 && origin[1] >= 0 && origin[2] >= 0), "ur_backward_slabs: origin must be >= 0");
+  UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_backward_slabs: bad shape kind");
+  UR_REQUIRE(shape->kind != UR_SHAPE_WEIGHTS || weights, "ur_backward_slabs: weights required for UR_SHAPE_WEIGHTS");
+  UR_REQUIRE(!weights || ((uintptr_t)weights % 8) == 0, "ur_backward_slabs: weights must be 8-byte aligned");
+  const size_t need = ur_workspace_size(p, UR_WS_FORWARD | UR_WS_ADJ_SLABS);
+  UR_REQUIRE(ws_bytes >= need, "ur_backward_slabs: workspace %zu < %zu bytes", ws_bytes, need);
+  UR_REQUIRE(((uintptr_t)ws % 256) == 0, "ur_backward_slabs: misaligned ws");
+  if (p->vsinc) {
+    ur_set_error("ur_backward_slabs: the adjoint of the voxel-sinc corrected binning is not built");
+    return UR_ERR_UNSUPPORTED;
+  }
+  if (dl_dmask_host) {
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, dl_dmask_host);
+    UR_REQUIRE(e == cudaSuccess && at.type == cudaMemoryTypeHost,
+               "ur_backward_slabs: dl_dmask_host must be page-locked host memory");
+  }
+  UR_TRY(ur_fault_point("backward"));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = p->n, H = p->H, nb = p->nbins, S = p->adj_slab_planes;
+  const double n3 = (double)n * n * n;
+  // workspace: [X][two host staging slabs][Y slab][sigma][two dL/dm staging slabs]
+  float2* X = (float2*)ws;
+  char* o = (char*)ws + ur_align_up(p->ws_inter, 256) + 2 * ur_align_up(p->ws_slab, 256);
+  float2* Ys = (float2*)o;
+  o += ur_align_up((size_t)S * n * H * sizeof(float2), 256);
+  float* sigma = (float*)o;
+  o += ur_align_up(p->ws_sigma, 256);
+  float* dm[2];
+  const size_t dm_bytes = (size_t)S * n * n * sizeof(float);
+  dm[0] = (float*)o;
+  dm[1] = (float*)(o + ur_align_up(dm_bytes, 256));
+
+  k_sigma<<<(nb + 255) / 256, 256, 0, s>>>(dl_dmean, fwd_bins, nb, n3, 0, sigma);
+  UR_LAUNCH_CHECK("k_sigma");
+  UR_CUDA_CHECK(cudaMemsetAsync(dl_dcell, 0, sizeof(float) * (size_t)ucell * ucell * ucell, s));
+  const int k2_zero = (int)(p->thr_host[nb] < 0x7fffffff ? p->thr_host[nb] : 0x7fffffff);
+
+  GradArgs g;
+  memset(&g, 0, sizeof g);
+  g.tw = p->tw;
+  g.stw = p->stw + p->stw_m_off;
+  g.cell = cell;
+  g.ucell = ucell;
+  if (origin) {
+    g.ox = origin[0] % ucell;
+    g.oy = origin[1] % ucell;
+    g.oz = origin[2] % ucell;
+  }
+  g.sh = ur_shape_args(shape);
+  g.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;
+  g.inv_n3 = (float)(1.0 / n3);
+  g.dl_dcell = dl_dcell;
+
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  ur_status st = UR_OK;
+  if (dl_dmask_host) {
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+      ok = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      ur_set_error("ur_backward_slabs: cannot create the copy stream or its events");
+      st = UR_ERR_CUDA;
+    }
+  }
+  int slab = 0;
+  for (int za = 0; za < n && st == UR_OK; za += S, ++slab) {
+    const int cnt = za + S <= n ? S : n - za;
+    const int b = slab & 1;
+    // z pass over every column, keeping planes [za, za + cnt)
+    ColArgs a = ur_col_args(p);
+    a.ncols = (long long)n * H;
+    a.A = H;
+    a.S = (long long)n * H;
+    a.Ad = H;
+    a.Sd = (long long)n * H;
+    a.src = X;
+    a.nload = p->nz;
+    a.zoff = p->z0;
+    a.dst = Ys;
+    a.sigma = sigma;
+    a.k2_zero = k2_zero;
+    a.out_lo = za;
+    a.out_cnt = cnt;
+    ur_timing_begin("adj_cols_z", s);
+    st = ur_fast_cols(n, 3 /* z adjoint */, a, s);
+    ur_timing_end(s);
+    if (st != UR_OK) break;
+    // y inverse of the slab, in place
+    ColArgs c = ur_col_args(p);
+    c.src = Ys;
+    c.dst = Ys;
+    c.ncols = (long long)cnt * H;
+    c.A = (long long)n * H;
+    c.S = H;
+    c.Ad = c.A;
+    c.Sd = c.S;
+    c.nload = n;
+    c.zoff = 0;
+    c.nbins = 0;
+    c.k2_zero = k2_zero;
+    ur_timing_begin("adj_cols_y", s);
+    st = ur_fast_cols(n, 1 /* y inverse */, c, s);
+    ur_timing_end(s);
+    if (st != UR_OK) break;
+    // rows: dL/du accumulated, dL/dm of the slab into staging buffer b
+    if (dl_dmask_host && slab >= 2) cudaStreamWaitEvent(s, freed[b], 0);
+    g.Y = Ys;
+    g.ybase_z = za;
+    g.z0 = za;
+    g.dl_dmask = dl_dmask_host ? dm[b] : nullptr;
+    g.mbase_z = za;
+    ur_timing_begin("adj_rows_grad", s);
+    st = ur_fast_rows_grad(n, g, cnt, s);
+    ur_timing_end(s);
+    if (st != UR_OK) break;
+    if (dl_dmask_host) {
+      cudaEventRecord(done[b], s);
+      cudaStreamWaitEvent(cs, done[b], 0);
+      const cudaError_t ce = cudaMemcpyAsync(dl_dmask_host + (size_t)za * n * n, dm[b], (size_t)cnt * n * n * sizeof(float),
+                                             cudaMemcpyDeviceToHost, cs);
+      if (ce != cudaSuccess) {
+        ur_set_error("ur_backward_slabs: dL/dm copy failed: %s", cudaGetErrorString(ce));
+        st = UR_ERR_CUDA;
+        break;
+      }
+      cudaEventRecord(freed[b], cs);
+    }
+  }
+  if (cs) {
+    // the caller's stream waits for the copies still queued
+    cudaEvent_t end;
+    if (cudaEventCreateWithFlags(&end, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(end, cs);
+      cudaStreamWaitEvent(s, end, 0);
+      cudaEventDestroy(end);
+    }
+    cudaStreamDestroy(cs);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (done[b]) cudaEventDestroy(done[b]);
+    if (freed[b]) cudaEventDestroy(freed[b]);
+  }
+  return st;
 }

@@ -99,6 +99,10 @@ extern "C" ur_status ur_batch_create(int32_t count, const ur_batch_item* items, 
     UR_REQUIRE(((uintptr_t)it.ws % 256) == 0, "ur_batch_create: item %d workspace misaligned", i);
     const bool bwd = it.dl_dmean && it.dl_dcell;
     has_bwd &= bwd ? 1 : 0;
+    if (bwd && p->vsinc) {
+      ur_set_error("ur_batch_create: item %d: the adjoint of the voxel-sinc corrected binning is not built", i);
+      return UR_ERR_UNSUPPORTED;
+    }
     const size_t need = ur_workspace_size(p, bwd ? (UR_WS_FORWARD | UR_WS_BACKWARD) : UR_WS_FORWARD);
     UR_REQUIRE(it.ws_bytes >= need, "ur_batch_create: item %d workspace %zu < %zu bytes", i, it.ws_bytes, need);
     const int n = p->n, H = p->H, M = p->M, nb = p->nbins;

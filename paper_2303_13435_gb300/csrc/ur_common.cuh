@@ -450,13 +450,25 @@ struct ur_plan {
   size_t ws_sigma;   // nbins floats (+pad)
   size_t ws_slab;    // one host-staging slab
   int slab_planes;
+  int adj_slab_planes;  // output planes per slab of the out-of-core adjoint (ur_backward_slabs)
   // power-of-two path
   int fast;          // 1: compile-time kernels (N a power of two in [64, 1024])
   int chunk_planes;  // planes per chunk of the plane pass / adjoint y and row passes (n: one launch each)
   size_t ws_chunk;   // adjoint chunk buffer (0 when chunk_planes = n: y-inverse in place)
+  float* vsinc;       // device [N/2+1] sinc^2(pi m/N) when the voxel-sinc correction is on, else NULL
+  // TMA z-column kernels (N = 256, 512; NULL otherwise)
+  float2* zc_tw;      // device [N/16][16]: W_N^(t k1)
+  int32_t* zc_tiles;  // device: tiles of 16 spectrum columns with a column below the closing threshold
+  int zc_ntiles;
 };
 
 // kernels launched from host code in other translation units
 ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s);
+// TMA z-column kernels (ur_zcol.cu)
+ur_status ur_zcol_prepare(ur_plan* p);
+bool ur_zcol_supported(const ur_plan* p);
+ur_status ur_zcol_forward(const ur_plan* p, const float2* X, double* bins, float2* F_out, float iscale, float fscale,
+                          cudaStream_t s);
+ur_status ur_deverr_take(void);
 
 static inline size_t ur_align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

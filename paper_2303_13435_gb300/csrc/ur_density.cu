@@ -25,10 +25,10 @@ __device__ __forceinline__ void store2<__half>(__half* out, float a, float b) {
 }
 
 // grid (ceil(N*N/2 / blockDim), z_count): each thread writes two neighbouring voxels of a row
-template <typename T>
+template <typename T, bool LAT>
 __global__ void __launch_bounds__(256) k_density(int N, const float* __restrict__ cell, int U, int ox, int oy, int oz,
-                                                 ShapeArgs sh, const float* __restrict__ weights, int z_begin,
-                                                 T* __restrict__ out, int* __restrict__ nz_range) {
+                                                 ShapeArgs sh, LatArgs lat, const float* __restrict__ weights,
+                                                 int z_begin, T* __restrict__ out, int* __restrict__ nz_range) {
   const int z = z_begin + blockIdx.y;
   const long long pair = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long plane_pairs = (long long)N * N / 2;
@@ -42,11 +42,13 @@ __global__ void __launch_bounds__(256) k_density(int N, const float* __restrict_
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int xx = x + e;
-      const float u = __ldg(crow + (xx + ox) % U);
+      const float u = LAT ? lattice_sample(lat, sh, cell, U, xx, y, z) : __ldg(crow + (xx + ox) % U);
       float m;
       if (sh.kind == UR_SHAPE_WEIGHTS) m = __ldg(weights + ((long long)z * N + y) * N + xx);
       else m = mask_at(sh, xx, y, z);
       v[e] = __fmul_rn(u, m);
+      // nonzero as stored (an FP16 value may round to zero)
+      if (sizeof(T) == 2) v[e] = __half2float(__float2half_rn(v[e]));
     }
     nonzero = (v[0] != 0.f) || (v[1] != 0.f);
     store2<T>(out + ((long long)blockIdx.y * N + y) * N + x, v[0], v[1]);
@@ -67,9 +69,9 @@ static ur_status shape_args(const ur_shape* shape, ShapeArgs* sh) {
   return UR_OK;
 }
 
-extern "C" ur_status ur_build_density(int32_t n, const float* cell, int32_t ucell, const int32_t* origin,
-                                      const ur_shape* shape, const float* weights, int32_t z_begin, int32_t z_count,
-                                      int32_t out_dtype, void* ed_out, int32_t* nz_range, void* stream) {
+static ur_status build_density(int32_t n, const float* cell, int32_t ucell, const int32_t* origin,
+                               const ur_lattice* lattice, const ur_shape* shape, const float* weights, int32_t z_begin,
+                               int32_t z_count, int32_t out_dtype, void* ed_out, int32_t* nz_range, void* stream) {
   UR_REQUIRE(n >= 2 && n % 2 == 0 && n <= 65536, "ur_build_density: grid edge %d must be even", n);
   UR_REQUIRE(cell && ed_out && ucell >= 1, "ur_build_density: null cell/output or empty cell");
   UR_REQUIRE(z_begin >= 0 && z_count >= 0 && z_begin + z_count <= n, "ur_build_density: planes [%d, %d) outside [0, %d)",
@@ -86,18 +88,43 @@ extern "C" ur_status ur_build_density(int32_t n, const float* cell, int32_t ucel
     oy = origin[1];
     oz = origin[2];
   }
+  const LatArgs lat = ur_lattice_args(lattice);
   if (z_count == 0) return UR_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const long long pairs = (long long)n * n / 2;
   dim3 grid((unsigned)((pairs + 255) / 256), (unsigned)z_count);
   ur_timing_begin("density", s);
-  if (out_dtype == UR_F32)
-    k_density<float><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, weights, z_begin, (float*)ed_out, nz_range);
+  if (out_dtype == UR_F32 && !lat.on)
+    k_density<float, false><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, lat, weights, z_begin, (float*)ed_out,
+                                                 nz_range);
+  else if (out_dtype == UR_F32)
+    k_density<float, true><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, lat, weights, z_begin, (float*)ed_out,
+                                                nz_range);
+  else if (!lat.on)
+    k_density<__half, false><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, lat, weights, z_begin,
+                                                  (__half*)ed_out, nz_range);
   else
-    k_density<__half><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, weights, z_begin, (__half*)ed_out, nz_range);
+    k_density<__half, true><<<grid, 256, 0, s>>>(n, cell, ucell, ox, oy, oz, sh, lat, weights, z_begin,
+                                                 (__half*)ed_out, nz_range);
   UR_LAUNCH_CHECK("k_density");
   ur_timing_end(s);
   return UR_OK;
+}
+
+extern "C" ur_status ur_build_density(int32_t n, const float* cell, int32_t ucell, const int32_t* origin,
+                                      const ur_shape* shape, const float* weights, int32_t z_begin, int32_t z_count,
+                                      int32_t out_dtype, void* ed_out, int32_t* nz_range, void* stream) {
+  return build_density(n, cell, ucell, origin, nullptr, shape, weights, z_begin, z_count, out_dtype, ed_out, nz_range,
+                       stream);
+}
+
+extern "C" ur_status ur_build_density_lattice(int32_t n, const float* cell, int32_t ucell, const ur_lattice* lattice,
+                                              const ur_shape* shape, const float* weights, int32_t z_begin,
+                                              int32_t z_count, int32_t out_dtype, void* ed_out, int32_t* nz_range,
+                                              void* stream) {
+  UR_REQUIRE(lattice, "ur_build_density_lattice: null lattice");
+  return build_density(n, cell, ucell, nullptr, lattice, shape, weights, z_begin, z_count, out_dtype, ed_out, nz_range,
+                       stream);
 }
 
 // ---------------------------------------------------------------------------

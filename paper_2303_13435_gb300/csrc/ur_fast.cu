@@ -174,26 +174,45 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows(RowArgs a) {
     }
     // rows the mask excludes entirely are zero (cell values are finite)
     if (valid && (wrow || !rm.empty())) {
-      const float* crow = a.cell + ((long long)a.fu.mod(z + a.oz) * U + a.fu.mod(y + a.oy)) * U;
-      // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
-      const int cstep = a.fu.mod(2 * T);
-      int c0 = a.fu.mod(2 * j + a.ox);
+      if constexpr (GEN == 2) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int x = 2 * (j + q * T);
-        float m0, m1;
-        if (wrow) {
-          const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
-          m0 = mw.x;
-          m1 = mw.y;
-        } else {
-          m0 = rm.at(x);
-          m1 = rm.at(x + 1);
+        for (int q = 0; q < 8; ++q) {
+          const int x = 2 * (j + q * T);
+          float m0, m1;
+          if (wrow) {
+            const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+            m0 = mw.x;
+            m1 = mw.y;
+          } else {
+            m0 = rm.at(x);
+            m1 = rm.at(x + 1);
+          }
+          const float u0 = m0 != 0.f ? lattice_sample(a.lat, a.sh, a.cell, U, x, y, z) : 0.f;
+          const float u1 = m1 != 0.f ? lattice_sample(a.lat, a.sh, a.cell, U, x + 1, y, z) : 0.f;
+          v[q] = make_float2(__fmul_rn(u0, m0), __fmul_rn(u1, m1));
         }
-        const float u0 = __ldg(crow + c0), u1 = __ldg(crow + (c0 + 1 == U ? 0 : c0 + 1));
-        c0 += cstep;
-        if (c0 >= U) c0 -= U;
-        v[q] = make_float2(__fmul_rn(u0, m0), __fmul_rn(u1, m1));
+      } else {
+        const float* crow = a.cell + ((long long)a.fu.mod(z + a.oz) * U + a.fu.mod(y + a.oy)) * U;
+        // cell column of x = 2 (j + q T): one modulo per thread, then steps of 2T mod U
+        const int cstep = a.fu.mod(2 * T);
+        int c0 = a.fu.mod(2 * j + a.ox);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int x = 2 * (j + q * T);
+          float m0, m1;
+          if (wrow) {
+            const float2 mw = __ldg(reinterpret_cast<const float2*>(wrow + x));
+            m0 = mw.x;
+            m1 = mw.y;
+          } else {
+            m0 = rm.at(x);
+            m1 = rm.at(x + 1);
+          }
+          const float u0 = __ldg(crow + c0), u1 = __ldg(crow + (c0 + 1 == U ? 0 : c0 + 1));
+          c0 += cstep;
+          if (c0 >= U) c0 -= U;
+          v[q] = make_float2(__fmul_rn(u0, m0), __fmul_rn(u1, m1));
+        }
       }
     }
   } else if (valid) {
@@ -427,11 +446,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       const int gcol = col0 + tc;
       const bool has = ch < NCH && gcol < a.ncols;
       int cc2 = 0, m0 = 0, bcur = 0;
-      float w = 0.f;
+      float w = 0.f, csc = a.iscale;  // csc: I scale of the column (times its voxel-sinc factor)
       if (has) {
         const int o2 = gcol / H, kx2 = gcol - o2 * H, ky2 = o2 < M ? o2 : o2 - N;
         cc2 = kx2 * kx2 + ky2 * ky2;
         w = (kx2 == 0 || kx2 == M) ? 1.f : 2.f;
+        if (a.vs) csc = a.iscale * (__ldg(a.vs + kx2) * __ldg(a.vs + (ky2 < 0 ? -ky2 : ky2)));
         m0 = ch * CH;
         const int s0 = cc2 + m0 * m0;
         bcur = s0 < thr[0] ? -1 : s0 >= thr[nb] ? nb : __ldg(a.lut + s0);
@@ -466,13 +486,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
                 tnext = b < nb ? thr[b + 1] : 0x7fffffff;
               } while (s >= tnext);
             }
+            const float sc = a.vs ? csc * __ldg(a.vs + mm) : csc;
             const float2 f1 = ln[p2pad(mm)];
-            const float i1 = (f1.x * f1.x + f1.y * f1.y) * a.iscale;
+            const float i1 = (f1.x * f1.x + f1.y * f1.y) * sc;
             sI += i1;
             sI2 += i1 * i1;
             if (mm != 0 && mm != M) {
               const float2 f2 = ln[p2pad(N - mm)];
-              const float i2 = (f2.x * f2.x + f2.y * f2.y) * a.iscale;
+              const float i2 = (f2.x * f2.x + f2.y * f2.y) * sc;
               sI += i2;
               sI2 += i2 * i2;
             }
@@ -504,8 +525,16 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     p2_fft<N, true>(v, j, line, a.stw);
     if (valid) {
       const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
+      if (a.out_cnt > 0) {  // a slab of output planes
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+        for (int q = 0; q < 8; ++q) {
+          const int zo = j + q * T - a.out_lo;
+          if (zo >= 0 && zo < a.out_cnt) a.dst[dbase + (long long)zo * a.Sd] = v[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+      }
     }
   }
 }
@@ -583,7 +612,7 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows_grad(GradArgs a) {
   rm.init(a.sh, valid ? y : 0, z);
   const float* wrow = a.weights ? a.weights + ((long long)z * N + (valid ? y : 0)) * N : nullptr;
   if (valid) {
-    float* drow = a.dl_dmask ? a.dl_dmask + ((long long)z * N + y) * N : nullptr;
+    float* drow = a.dl_dmask ? a.dl_dmask + ((long long)(z - a.mbase_z) * N + y) * N : nullptr;
     // rows the mask excludes entirely add nothing to dL/du
     const bool mzero = !wrow && rm.empty();
     // cell columns of x = 2 (j + q T): one modulo, then steps of 2T mod U; when U divides
@@ -701,7 +730,8 @@ static ur_status launch_rows_n(const RowArgs& a, int gen, int ed_f16, cudaStream
   constexpr int M = N / 2, T = M / 8, RB = 512 / T;
   const int grid = (int)((a.nrows + RB - 1) / RB);
   if (grid <= 0) return UR_OK;
-  if (gen) k_p2_rows<N, 1, float><<<grid, 512, 0, s>>>(a);
+  if (gen == 2) k_p2_rows<N, 2, float><<<grid, 512, 0, s>>>(a);
+  else if (gen) k_p2_rows<N, 1, float><<<grid, 512, 0, s>>>(a);
   else if (ed_f16) k_p2_rows<N, 0, __half><<<grid, 512, 0, s>>>(a);
   else k_p2_rows<N, 0, float><<<grid, 512, 0, s>>>(a);
   UR_LAUNCH_CHECK("k_p2_rows");

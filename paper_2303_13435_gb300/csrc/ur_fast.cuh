@@ -13,7 +13,8 @@ struct RowArgs {
   int ucell, ox, oy, oz;   // origin >= 0
   FastDiv fu;              // division by ucell
   ShapeArgs sh;
-  const float* weights;    // GEN = 1 with UR_SHAPE_WEIGHTS: full-box weights
+  LatArgs lat;             // GEN = 2: the cell sampled on a rotated lattice
+  const float* weights;    // GEN >= 1 with UR_SHAPE_WEIGHTS: full-box weights
   const float2* tw;        // table exp(-2 pi i t / N), t < N
   const float2* stw;       // stage twiddles of the N/2-point transform (power-of-two kernels)
   int skip_empty;          // GEN = 1, sphere, N <= 512: rows outside the particle are not written
@@ -32,7 +33,8 @@ struct GradArgs {
   ShapeArgs sh;
   const float* weights;
   float inv_n3;
-  float* dl_dmask;
+  float* dl_dmask;         // dL/dm planes from mbase_z on (plane z at z - mbase_z)
+  int mbase_z;
   float* dl_dcell;
 };
 

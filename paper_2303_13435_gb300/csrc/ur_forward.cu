@@ -73,7 +73,11 @@ __device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, 
           m0 = mask_at(ra.sh, x, y, z);
           m1 = mask_at(ra.sh, x + 1, y, z);
         }
-        v = make_float2(__fmul_rn(__ldg(crow + (x + ra.ox) % U), m0), __fmul_rn(__ldg(crow + (x + 1 + ra.ox) % U), m1));
+        if (GEN == 2)
+          v = make_float2(__fmul_rn(lattice_sample(ra.lat, ra.sh, ra.cell, U, x, y, z), m0),
+                          __fmul_rn(lattice_sample(ra.lat, ra.sh, ra.cell, U, x + 1, y, z), m1));
+        else
+          v = make_float2(__fmul_rn(__ldg(crow + (x + ra.ox) % U), m0), __fmul_rn(__ldg(crow + (x + 1 + ra.ox) % U), m1));
       } else {
         v = load_pair<T>(ed + r * N + 2 * m);
       }
@@ -162,7 +166,9 @@ __device__ __forceinline__ void walk_bins(const ColArgs& a, const int32_t* __res
     const int m0 = ch * BIN_CHUNK;
     const int m1 = min(m0 + BIN_CHUNK, M + 1);
     int cur = bin_search(thr, a.nbins, c2 + m0 * m0);
-    op.begin(cur);
+    // voxel-sinc factor of the column (kx, ky); the kz part is applied per element
+    const float cs = a.vs ? __ldg(a.vs + kx) * __ldg(a.vs + (ky < 0 ? -ky : ky)) : 1.f;
+    op.begin(cur, cs);
     for (int m = m0; m < m1; ++m) {
       const int s = c2 + m * m;
       while (cur < a.nbins && thr[cur + 1] <= s) ++cur;
@@ -180,6 +186,8 @@ struct BinAccum {
   double* hs2;
   int run;
   float aI, aI2;
+  const float* vs;
+  float cs;
   __device__ __forceinline__ void flush(float w) {
     if (run >= 0 && run < nbins && (aI != 0.f || aI2 != 0.f)) {
       atomicAdd(hs + run, (double)(w * aI));
@@ -188,22 +196,24 @@ struct BinAccum {
     aI = 0.f;
     aI2 = 0.f;
   }
-  __device__ __forceinline__ void begin(int b) {
+  __device__ __forceinline__ void begin(int b, float c) {
     run = b;
     aI = 0.f;
     aI2 = 0.f;
+    cs = c;
   }
   __device__ __forceinline__ void visit(int t, int m, int b, float w) {
     if (b != run) {
       flush(w);
       run = b;
     }
+    const float sc = vs ? iscale * (cs * __ldg(vs + m)) : iscale;
     const float2 f1 = buf[t * pitch + m];
-    const float i1 = (f1.x * f1.x + f1.y * f1.y) * iscale;
+    const float i1 = (f1.x * f1.x + f1.y * f1.y) * sc;
     float s = i1, s2 = i1 * i1;
     if (m != 0 && m != M) {
       const float2 f2 = buf[t * pitch + N - m];
-      const float i2 = (f2.x * f2.x + f2.y * f2.y) * iscale;
+      const float i2 = (f2.x * f2.x + f2.y * f2.y) * sc;
       s += i2;
       s2 += i2 * i2;
     }
@@ -217,7 +227,7 @@ struct SigmaScale {
   float2* buf;
   int pitch, M, N, nbins;
   const float* sigma;
-  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void begin(int, float) {}
   __device__ __forceinline__ void end(float) {}
   __device__ __forceinline__ void visit(int t, int m, int b, float) {
     const float sg = (b >= 0 && b < nbins) ? __ldg(sigma + b) : 0.f;
@@ -285,7 +295,7 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
         }
       }
       if (a.nbins > 0) {
-        BinAccum acc{buf, a.pitch, a.M, N, a.nbins, a.iscale, hs, hs2, -1, 0.f, 0.f};
+        BinAccum acc{buf, a.pitch, a.M, N, a.nbins, a.iscale, hs, hs2, -1, 0.f, 0.f, a.vs, 1.f};
         walk_bins(a, thr, c0, acc);
       }
     } else {  // COL_ZADJ: F along z (recomputed or given), times sigma(bin), inverse along z
@@ -455,7 +465,8 @@ ur_status ur_launch_geometry(ur_plan* p, cudaStream_t s) {
 // Standalone binning of a stored half-spectrum intensity (Sec. 2.5)
 // ---------------------------------------------------------------------------
 __global__ void k_bin_half(const float* __restrict__ I, int N, const int32_t* __restrict__ thr_g, int nb,
-                           double* __restrict__ gsum, double* __restrict__ gsum2, double scale) {
+                           double* __restrict__ gsum, double* __restrict__ gsum2, double scale,
+                           const float* __restrict__ vs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   int32_t* thr = reinterpret_cast<int32_t*>(smraw);
   double* hs = reinterpret_cast<double*>(smraw + ur_align_up_dev((size_t)(nb + 1) * 4, 16));
@@ -476,7 +487,8 @@ __global__ void k_bin_half(const float* __restrict__ I, int N, const int32_t* __
     const int b = bin_search(thr, nb, s);
     if (b >= 0 && b < nb) {
       const double w = (kx == 0 || kx == M) ? 1.0 : 2.0;
-      const double v = (double)I[e] * scale;
+      double v = (double)I[e] * scale;
+      if (vs) v *= (double)(__ldg(vs + kx) * __ldg(vs + (ky < 0 ? -ky : ky)) * __ldg(vs + (kz < 0 ? -kz : kz)));
       atomicAdd(hs + b, w * v);
       atomicAdd(hs2 + b, w * v * v);
     }
@@ -521,6 +533,7 @@ ur_status ur_configure_kernels(ur_plan* p) {
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<0, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
+  UR_CUDA_CHECK(cudaFuncSetAttribute(k_rows_r2c<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
   UR_CUDA_CHECK(cudaFuncSetAttribute(k_cols<COL_ZBIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
@@ -543,6 +556,13 @@ ur_status ur_configure_kernels(ur_plan* p) {
     if (sp > p->nz) sp = p->nz;
     p->slab_planes = (int)sp;
     p->ws_slab = (size_t)sp * ed_plane;
+  }
+  // out-of-core adjoint: about 4 GiB of inverse intermediate per slab
+  {
+    long long ap = (long long)((4ull << 30) / ((size_t)n * p->H * sizeof(float2)));
+    if (ap < 1) ap = 1;
+    if (ap > n) ap = n;
+    p->adj_slab_planes = (int)ap;
   }
   // power-of-two kernels; by default every pass runs over all planes at once
   // (ur_plan_set_chunk_planes can split the plane pass and the adjoint's y and
@@ -580,6 +600,7 @@ ColArgs ur_col_args(const ur_plan* p) {
   a.thr = p->thr;
   a.lut = p->binlut;
   a.k2_zero = 0x7fffffff;
+  a.vs = p->vsinc;
   a.crs = p->bincoarse;
   a.crs_shift = p->coarse_shift;
   a.nbins = p->nbins;
@@ -613,7 +634,8 @@ static ur_status plane_pass(const ur_plan* p, RowArgs ra, int gen, long long npl
     } else {
       const int grid_rows = (int)((r.nrows + p->row_rb - 1) / p->row_rb);
       const StageInfo* sm = p->d_sched + UR_MAX_STAGES;
-      if (gen) k_rows_r2c<1, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
+      if (gen == 2) k_rows_r2c<2, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
+      else if (gen) k_rows_r2c<1, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
       else if (p->ed_dtype == UR_F32)
         k_rows_r2c<0, float><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
       else k_rows_r2c<0, __half><<<grid_rows, p->row_threads, p->row_smem, s>>>(r, n, p->row_rb, sm, p->sched_m.nst);
@@ -679,15 +701,19 @@ ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2
   } else {
     a.nbins = 0;
   }
+  // power-of-two grids of 256 and 512 with binning: the TMA z-column kernel
+  const bool zc = bins && p->fast && ur_zcol_supported(p);
   ur_timing_begin("cols_z_bin", s);
-  if (p->fast) {
+  if (zc) {
+    UR_TRY(ur_zcol_forward(p, X, bins, F_out, a.iscale, a.fscale, s));
+  } else if (p->fast) {
     UR_TRY(ur_fast_cols(p->n, 2 /* z + bins */, a, s));
   } else {
     k_cols<COL_ZBIN, false><<<p->zbin_grid, p->col_threads, p->colbin_smem, s>>>(a);
     UR_LAUNCH_CHECK("k_cols<COL_ZBIN>");
   }
   ur_timing_end(s);
-  if (bins) {
+  if (bins && !zc) {  // (the TMA z-column kernel finalizes the bins itself)
     ur_timing_begin("finalize", s);
     k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
     UR_LAUNCH_CHECK("k_finalize");
@@ -711,9 +737,9 @@ extern "C" ur_status ur_fft_intensity(const ur_plan* p, const void* ed, int32_t 
   return UR_OK;
 }
 
-extern "C" ur_status ur_fft_intensity_tiled(const ur_plan* p, const float* cell, int32_t ucell, const int32_t* origin,
-                                            const ur_shape* shape, const float* weights, double* bins, void* F_out,
-                                            void* ws, size_t ws_bytes, void* stream) {
+static ur_status fft_intensity_tiled(const ur_plan* p, const float* cell, int32_t ucell, const int32_t* origin,
+                                     const ur_lattice* lattice, const ur_shape* shape, const float* weights,
+                                     double* bins, void* F_out, void* ws, size_t ws_bytes, void* stream) {
   UR_REQUIRE(p && cell && shape && ws, "ur_fft_intensity_tiled: null argument");
   UR_REQUIRE(ucell >= 1, "ur_fft_intensity_tiled: empty cell");
   UR_REQUIRE(shape->kind >= UR_SHAPE_SPHERE && shape->kind <= UR_SHAPE_WEIGHTS, "ur_fft_intensity_tiled: bad shape kind");
@@ -737,11 +763,26 @@ extern "C" ur_status ur_fft_intensity_tiled(const ur_plan* p, const float* cell,
     ra.oz = origin[2];
   }
   ra.sh = ur_shape_args(shape);
+  ra.lat = ur_lattice_args(lattice);
   ra.weights = shape->kind == UR_SHAPE_WEIGHTS ? weights : nullptr;
   float2* X = (float2*)ws;
-  UR_TRY(plane_pass(p, ra, 1, p->nz, X, s));
+  UR_TRY(plane_pass(p, ra, lattice ? 2 : 1, p->nz, X, s));
   UR_TRY(ur_column_pass(p, X, bins, (float2*)F_out, s));
   return UR_OK;
+}
+
+extern "C" ur_status ur_fft_intensity_tiled(const ur_plan* p, const float* cell, int32_t ucell, const int32_t* origin,
+                                            const ur_shape* shape, const float* weights, double* bins, void* F_out,
+                                            void* ws, size_t ws_bytes, void* stream) {
+  return fft_intensity_tiled(p, cell, ucell, origin, nullptr, shape, weights, bins, F_out, ws, ws_bytes, stream);
+}
+
+extern "C" ur_status ur_fft_intensity_tiled_lattice(const ur_plan* p, const float* cell, int32_t ucell,
+                                                    const ur_lattice* lattice, const ur_shape* shape,
+                                                    const float* weights, double* bins, void* F_out, void* ws,
+                                                    size_t ws_bytes, void* stream) {
+  UR_REQUIRE(lattice, "ur_fft_intensity_tiled_lattice: null lattice");
+  return fft_intensity_tiled(p, cell, ucell, nullptr, lattice, shape, weights, bins, F_out, ws, ws_bytes, stream);
 }
 
 extern "C" ur_status ur_bin_q(const ur_plan* p, const float* I, double* bins, void* ws, size_t ws_bytes, void* stream) {
@@ -755,7 +796,8 @@ extern "C" ur_status ur_bin_q(const ur_plan* p, const float* I, double* bins, vo
   UR_CUDA_CHECK(cudaMemsetAsync(bins, 0, sizeof(double) * UR_BIN_FIELDS * nb, s));
   const double n3 = (double)p->n * p->n * p->n;
   // the kernel accumulates I * N^3 so that k_finalize's I' convention applies
-  k_bin_half<<<p->num_sms * 4, 256, smem, s>>>(I, p->n, p->thr, nb, bins + UR_BIN_SUM_I * nb, bins + UR_BIN_SUM_I2 * nb, n3);
+  k_bin_half<<<p->num_sms * 4, 256, smem, s>>>(I, p->n, p->thr, nb, bins + UR_BIN_SUM_I * nb, bins + UR_BIN_SUM_I2 * nb, n3,
+                                               p->vsinc);
   UR_LAUNCH_CHECK("k_bin_half");
   k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
   UR_LAUNCH_CHECK("k_finalize");

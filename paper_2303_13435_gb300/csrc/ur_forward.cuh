@@ -34,6 +34,7 @@ struct ColArgs {
   int crs_shift;
   int nbins;
   float iscale;      // I' = |F~|^2 * iscale (I' = N^3 I)
+  const float* vs;   // voxel-sinc factors sinc^2(pi m / N), m = 0..N/2, or NULL (binning of plain |F|^2)
   double* gsum;      // [nbins] sum of w I'
   double* gsum2;     // [nbins] sum of w I'^2
   float2* fout;      // optional F half spectrum [kz][ky][kx]
@@ -44,6 +45,8 @@ struct ColArgs {
   int row_skip;        // power-of-two forward y pass over a generated sphere density: rows
   int gen_z0;          // (y, gen_z0 + plane) outside the sphere are zero and were not
   ShapeArgs sh;        // written by the row pass; they are not read
+  int out_lo, out_cnt; // adjoint z pass: write only the planes z in [out_lo, out_lo + out_cnt), at
+                       // z - out_lo (out_cnt = 0: every plane)
   int k2_zero;         // power-of-two adjoint: spectrum columns with kx^2 + ky^2 >= k2_zero are
                        // zero; the z pass may leave them unwritten and the y pass does not read
                        // them (0x7fffffff: none)

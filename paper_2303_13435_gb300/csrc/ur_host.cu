@@ -67,7 +67,8 @@ extern "C" ur_status ur_sync_status(void* stream) {
     ur_set_error("ur_sync_status: %s", cudaGetErrorString(e));
     return UR_ERR_CUDA;
   }
-  return UR_OK;
+  // bounded device-side waits that gave up leave a word behind
+  return ur_deverr_take();
 }
 
 extern "C" void ur_fault_reset(void) {
@@ -306,6 +307,9 @@ static void plan_free(ur_plan* p) {
   if (p->d_sched) cudaFree(p->d_sched);
   if (p->binlut) cudaFree(p->binlut);
   if (p->bincoarse) cudaFree(p->bincoarse);
+  if (p->zc_tw) cudaFree(p->zc_tw);
+  if (p->vsinc) cudaFree(p->vsinc);
+  if (p->zc_tiles) cudaFree(p->zc_tiles);
   free(p->thr_host);
   free(p);
 }
@@ -427,6 +431,7 @@ extern "C" ur_status ur_plan_create(const ur_grid_desc* g, const double* edges, 
       st = UR_ERR_CUDA;
     }
   }
+  if (st == UR_OK) st = ur_zcol_prepare(p);
   if (st != UR_OK) {
     plan_free(p);
     return st;
@@ -434,6 +439,36 @@ extern "C" ur_status ur_plan_create(const ur_grid_desc* g, const double* edges, 
   *out = p;
   return UR_OK;
 }
+
+extern "C" ur_status ur_plan_set_voxel_sinc(ur_plan* p, int32_t on) {
+  UR_REQUIRE(p, "ur_plan_set_voxel_sinc: null plan");
+  if (!on) {
+    if (p->vsinc) cudaFree(p->vsinc);
+    p->vsinc = nullptr;
+    return UR_OK;
+  }
+  if (p->vsinc) return UR_OK;
+  const int M = p->M;
+  float* h = (float*)malloc(sizeof(float) * (M + 1));
+  for (int m = 0; m <= M; ++m) {
+    const double a = M_PI * (double)m / (double)p->n;
+    const double sn = m == 0 ? 1.0 : sin(a) / a;
+    h[m] = (float)(sn * sn);
+  }
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(float) * (M + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(d, h, sizeof(float) * (M + 1), cudaMemcpyHostToDevice);
+  free(h);
+  if (e != cudaSuccess) {
+    if (d) cudaFree(d);
+    ur_set_error("ur_plan_set_voxel_sinc: %s", cudaGetErrorString(e));
+    return UR_ERR_OOM;
+  }
+  p->vsinc = d;
+  return UR_OK;
+}
+
+extern "C" int32_t ur_plan_voxel_sinc(const ur_plan* p) { return (p && p->vsinc) ? 1 : 0; }
 
 extern "C" ur_status ur_plan_destroy(ur_plan* p) {
   plan_free(p);
@@ -453,6 +488,13 @@ extern "C" size_t ur_workspace_size(const ur_plan* p, int32_t what) {
   if (what & UR_WS_BACKWARD)
     b += ur_align_up(p->ws_inv, 256) + ur_align_up(p->ws_sigma, 256) + ur_align_up(p->ws_chunk, 256);
   if (what & UR_WS_HOST_SLABS) b += 2 * ur_align_up(p->ws_slab, 256);
+  if (what & UR_WS_ADJ_SLABS) {
+    // fixed layout after the forward intermediate: [host staging slabs][Y slab][sigma][two dL/dm slabs]
+    const size_t S = (size_t)p->adj_slab_planes;
+    if (!(what & UR_WS_HOST_SLABS)) b += 2 * ur_align_up(p->ws_slab, 256);
+    b += ur_align_up(S * p->n * p->H * sizeof(float2), 256) + ur_align_up(p->ws_sigma, 256) +
+         2 * ur_align_up(S * p->n * p->n * sizeof(float), 256);
+  }
   return b;
 }
 
@@ -583,4 +625,119 @@ extern "C" ur_status ur_merge(int32_t nlev, const double* const* level_bins, con
   k_merge<<<(nbins + 127) / 128, 128, 0, s>>>(a, edges, nbins, out);
   UR_LAUNCH_CHECK("k_merge");
   return UR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Polydisperse ensemble (Sec. 3: volume-weighted single-particle simulations summed
+// into one curve): one thread per bin.  The item tables travel as kernel parameters
+// (by value, so the launch can be captured in a CUDA graph).
+// ---------------------------------------------------------------------------
+#define UR_MAX_ENSEMBLE 512
+struct EnsembleArgs {
+  const double* bins[UR_MAX_ENSEMBLE];
+  double* grad[UR_MAX_ENSEMBLE];
+  double scale[UR_MAX_ENSEMBLE];  // w_i N_i^6
+  int count;
+};
+
+__device__ __forceinline__ bool ens_valid(const EnsembleArgs& a, int nb, int j) {
+  for (int i = 0; i < a.count; ++i)
+    if (a.scale[i] != 0.0 && !(a.bins[i][UR_BIN_COUNT * nb + j] > 0)) return false;
+  return true;
+}
+
+__global__ void k_ensemble(const __grid_constant__ EnsembleArgs a, int nb, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double mean = nan, sem = nan, cnt = 0.0, q = nan;
+  if (ens_valid(a, nb, j)) {
+    double s = 0.0, v = 0.0, c = 0.0, cq = 0.0;
+    for (int i = 0; i < a.count; ++i) {
+      const double sc = a.scale[i];
+      if (sc == 0.0) continue;
+      const double* b = a.bins[i];
+      s += sc * b[UR_BIN_MEAN * nb + j];
+      const double e = sc * b[UR_BIN_SEM * nb + j];
+      v += e * e;
+      c += b[UR_BIN_COUNT * nb + j];
+      cq += b[UR_BIN_SUM_Q * nb + j];
+    }
+    mean = s;
+    sem = sqrt(v);
+    cnt = c;
+    q = cq / c;
+  }
+  out[0 * nb + j] = mean;
+  out[1 * nb + j] = sem;
+  out[2 * nb + j] = cnt;
+  out[3 * nb + j] = q;
+}
+
+__global__ void k_ensemble_grad(const __grid_constant__ EnsembleArgs a, int nb, const double* __restrict__ g) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const bool ok = ens_valid(a, nb, j) && isfinite(g[j]);
+  for (int i = 0; i < a.count; ++i) a.grad[i][j] = ok ? a.scale[i] * g[j] : 0.0;
+}
+
+static ur_status ensemble_args(int32_t count, const double* const* item_bins, const int32_t* item_n,
+                               const double* weights, double* const* item_grad, EnsembleArgs* a) {
+  UR_REQUIRE(count >= 1 && count <= UR_MAX_ENSEMBLE, "ensemble: %d items (1..%d)", count, UR_MAX_ENSEMBLE);
+  UR_REQUIRE(item_bins && item_n && weights, "ensemble: null argument");
+  memset(a, 0, sizeof *a);
+  a->count = count;
+  for (int i = 0; i < count; ++i) {
+    UR_REQUIRE(item_bins[i] && item_n[i] > 0 && isfinite(weights[i]),
+               "ensemble: item %d has no bins, a bad size or a non-finite weight", i);
+    UR_REQUIRE(!item_grad || item_grad[i], "ensemble: item %d has no gradient output", i);
+    a->bins[i] = item_bins[i];
+    a->grad[i] = item_grad ? item_grad[i] : nullptr;
+    const double nn = (double)item_n[i];
+    a->scale[i] = weights[i] * nn * nn * nn * nn * nn * nn;
+  }
+  return UR_OK;
+}
+
+extern "C" ur_status ur_ensemble(int32_t count, const double* const* item_bins, const int32_t* item_n,
+                                 const double* weights, int32_t nbins, double* out, void* stream) {
+  UR_REQUIRE(nbins >= 1 && out, "ur_ensemble: bad argument");
+  EnsembleArgs* a = (EnsembleArgs*)malloc(sizeof(EnsembleArgs));
+  if (!a) {
+    ur_set_error("ur_ensemble: out of host memory");
+    return UR_ERR_OOM;
+  }
+  ur_status st = ensemble_args(count, item_bins, item_n, weights, nullptr, a);
+  if (st == UR_OK) {
+    k_ensemble<<<(nbins + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*a, nbins, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ur_set_error("launch of k_ensemble failed: %s", cudaGetErrorString(e));
+      st = UR_ERR_CUDA;
+    }
+  }
+  free(a);
+  return st;
+}
+
+extern "C" ur_status ur_ensemble_backward(int32_t count, const double* const* item_bins, const int32_t* item_n,
+                                          const double* weights, int32_t nbins, const double* dl_dens,
+                                          double* const* item_dl_dmean, void* stream) {
+  UR_REQUIRE(nbins >= 1 && dl_dens && item_dl_dmean, "ur_ensemble_backward: bad argument");
+  EnsembleArgs* a = (EnsembleArgs*)malloc(sizeof(EnsembleArgs));
+  if (!a) {
+    ur_set_error("ur_ensemble_backward: out of host memory");
+    return UR_ERR_OOM;
+  }
+  ur_status st = ensemble_args(count, item_bins, item_n, weights, item_dl_dmean, a);
+  if (st == UR_OK) {
+    k_ensemble_grad<<<(nbins + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*a, nbins, dl_dens);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ur_set_error("launch of k_ensemble_grad failed: %s", cudaGetErrorString(e));
+      st = UR_ERR_CUDA;
+    }
+  }
+  free(a);
+  return st;
 }

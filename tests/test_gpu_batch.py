@@ -121,3 +121,47 @@ def test_autotuner_sets_tiles_and_keeps_results():
         ok = x[0] > 0
         assert np.allclose(x[4][ok], y[4][ok], rtol=MEAN_RTOL, atol=0)
     assert len(before) == len(plans)
+
+
+def test_polydisperse_ensemble_on_the_batch_matches_oracle_and_its_gradient_flows():
+    """Sec. 3 polydispersity: the volume-weighted ensemble of the batch's particle curves
+    (ur_ensemble) against the oracle's ensemble of the oracle's particle curves, and the
+    ensemble adjoint (ur_ensemble_backward) feeding the batch adjoint against the oracle's
+    chain rule through the weights."""
+    from oracle import merge as omerge, scatter
+    parts, plans, rhos, cell, cell_np, edges = _setup(count=5, lo=64, hi=96, nbins=48)
+    batch = api.Batch(plans, cell, [p.shape for p in parts])
+    batch.forward()
+    vols = [float((r != 0).sum()) * DX ** 3 for r in rhos]
+    w = np.array([0.2 / v for v in vols])
+    ens = api.ensemble(batch.bins, [p.n for p in parts], w).cpu().numpy()
+    items = []
+    for p, r in zip(parts, rhos):
+        ob = oracle_forward(r.astype(np.float64), DX, edges)
+        items.append({"n": p.n, "count": ob["count"], "mean": ob["mean"], "sem": ob["sem"], "mean_q": ob["mean_q"]})
+    want = omerge.ensemble_sum(items, w)
+    ok = want["count"] > 0
+    assert ok.sum() > 10
+    assert np.array_equal(ens[2][ok].astype(np.int64), want["count"][ok])
+    assert np.all(np.isnan(ens[0][~ok]))
+    assert np.max(np.abs(ens[0][ok] / want["mean"][ok] - 1)) <= MEAN_RTOL
+    # the kernel's arithmetic against the oracle's on identical inputs (the GPU item curves)
+    gi = [{"n": p.n, "count": b[0].astype(np.int64), "mean": b[4], "sem": b[5], "mean_q": b[3] / np.maximum(b[0], 1)}
+          for p, b in zip(parts, [x.cpu().numpy() for x in batch.bins])]
+    same = omerge.ensemble_sum(gi, w)
+    assert np.allclose(ens[0][ok], same["mean"][ok], rtol=1e-13, atol=0)
+    assert np.allclose(ens[1][ok], same["sem"][ok], rtol=1e-13, atol=0)
+    # gradient: dL/dmean_i = w_i N_i^6 dL/dens on valid bins
+    g = torch.from_numpy(np.where(ok, 1.0 / np.where(ok, want["mean"], 1.0), 0.0)).cuda()
+    api.ensemble_backward(batch.bins, [p.n for p in parts], w, g, batch.dl_dmean)
+    gn = g.cpu().numpy()
+    for i, p in enumerate(parts):
+        d = batch.dl_dmean[i].cpu().numpy()
+        assert np.allclose(d, np.where(ok, w[i] * float(p.n) ** 6 * gn, 0.0), rtol=1e-14, atol=0)
+    batch.backward()
+    torch.cuda.synchronize()
+    for i, (p, r) in enumerate(zip(parts, rhos)):
+        gu, _ = oracle_grads(r.astype(np.float64), cell_np.astype(np.float64),
+                             density.mask_values(p.n, p.shape.kind, p.shape.center, p.shape.size, p.shape.rot)
+                             .astype(np.float64), DX, edges, batch.dl_dmean[i].cpu().numpy(), items[i]["count"])
+        assert normwise(batch.dl_dcell[i].cpu().numpy(), gu) <= GRAD_RTOL

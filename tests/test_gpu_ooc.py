@@ -115,3 +115,103 @@ def test_streamed_2048_cube_parseval_counts_and_device_path():
     ref = api.fft_intensity(plan, dev).cpu().numpy()
     assert np.array_equal(bins[0], ref[0])
     assert np.allclose(bins[1:4], ref[1:4], rtol=2e-5, atol=0)
+
+
+def test_streamed_1024_sampled_k_against_direct_eq1():
+    """The streamed path at 1024^3 (density in pinned host memory, small slabs) against
+    Eq. 1 summed directly by the oracle at sampled frequencies (oracle.scatter.dft_at over
+    the nonzero planes): F_out at 24 seeded k, including k = 0 and both Nyquist faces."""
+    from oracle import scatter
+    n = 1024
+    w = _sphere(n, 500, nbins=64)
+    rho = oracle_density(w)
+    z0, nz = _slab(rho)
+    plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
+    plan.set_slab_planes(37)
+    host = torch.from_numpy(np.ascontiguousarray(rho[z0:z0 + nz])).pin_memory()
+    H = n // 2 + 1
+    F = torch.empty((n, n, H), dtype=torch.complex64, device="cuda")
+    api.fft_intensity(plan, host, F_out=F)
+    rng = np.random.default_rng(2048)
+    ks = [(0, 0, 0), (512, 0, 0), (0, -512, 0), (0, 0, -512), (3, -7, 11)]
+    ks += [(int(rng.integers(0, H)), int(rng.integers(-512, 512)), int(rng.integers(-512, 512))) for _ in range(19)]
+    ks = np.array(ks, dtype=np.int64)
+    want = scatter.dft_at(rho[z0:z0 + nz], ks, z_begin=z0)
+    Fh = F.cpu().numpy()
+    got = np.array([Fh[kz % n, ky % n, kx] for kx, ky, kz in ks])
+    tol = 1e-4 * np.abs(want) + 1e-6 * abs(want[0])
+    assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want) / tol)
+
+
+@pytest.mark.parametrize("slab", [37, 256])
+def test_slab_adjoint_equals_device_adjoint(slab):
+    """Out-of-core adjoint (ur_backward_slabs, z pass recomputed per slab of output planes,
+    dL/dm copied to pinned host memory) against the device-resident ur_backward on the same
+    forward: same kernels, so dL/du and dL/dm agree to FP32 accumulation order; the forward
+    ran from pinned host memory (streamed), so the whole out-of-core step is covered."""
+    w = _sphere(256, 110, nbins=96)
+    rho = oracle_density(w)
+    z0, nz = _slab(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    plan.set_slab_planes(29)
+    plan.set_adj_slab_planes(slab)
+    cell = torch.from_numpy(w.cell).cuda()
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_HOST_SLABS | api.UR_WS_ADJ_SLABS)
+    host = torch.from_numpy(np.ascontiguousarray(rho[z0:z0 + nz])).pin_memory()
+    bins = api.fft_intensity(plan, host, ws=ws)
+    m = bins[4]
+    g = torch.where(torch.isfinite(m) & (m > 0), 1e-3 / torch.nan_to_num(m, nan=1.0).clamp(min=1e-300), 0.0)
+    dm_host = torch.empty((w.n, w.n, w.n), dtype=torch.float32).pin_memory()
+    dc_s, _ = api.backward_slabs(plan, g, bins, cell, w.shape, ws, dl_dmask_host=dm_host)
+    api.sync_status()
+    ws2 = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    api.fft_intensity(plan, host.cuda(), ws=ws2)
+    dc_d, dm_d = api.backward(plan, g, bins, cell, w.shape, ws2)
+    torch.cuda.synchronize()
+    a, b = dc_s.cpu().numpy(), dc_d.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+    a, b = dm_host.numpy(), dm_d.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
+def test_slab_adjoint_2048_directional_derivative():
+    """2048^3 streamed forward (density in pinned host memory) and the slab adjoint: for
+    L = sum_j c_j mean_j the central difference of the streamed forward in the cell equals
+    <dL/du, d> up to rounding (no N^3 inverse intermediate is ever held)."""
+    n = 2048
+    w = _sphere(n, 820, nbins=200)
+    cell = torch.from_numpy(w.cell).cuda()
+    rng = torch.tensor([2 ** 31 - 1, -1], dtype=torch.int32, device="cuda")
+    z_lo = n // 2 - 420
+    probe = api.build_density(n, cell, w.shape, z_begin=z_lo, z_count=840, nz_range=rng)
+    del probe
+    z0, z1 = rng.cpu().tolist()
+    nz = z1 - z0 + 1
+    plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
+    plan.set_adj_slab_planes(300)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_HOST_SLABS | api.UR_WS_ADJ_SLABS)
+    host = torch.empty((nz, n, n), dtype=torch.float32, pin_memory=True)
+
+    def fill(cc):
+        for p0 in range(0, nz, 64):
+            cnt = min(64, nz - p0)
+            host[p0:p0 + cnt].copy_(api.build_density(n, cc, w.shape, z_begin=z0 + p0, z_count=cnt))
+        torch.cuda.synchronize()
+
+    fill(cell)
+    b0 = api.fft_intensity(plan, host, ws=ws)
+    m0 = b0[4].double()
+    c = torch.where(torch.isfinite(m0) & (m0 > 0), 1.0 / torch.nan_to_num(m0, nan=1.0).clamp(min=1e-300), 0.0)
+    dcell, _ = api.backward_slabs(plan, c, b0, cell, w.shape, ws)
+    api.sync_status()
+
+    def loss(cc):
+        fill(cc)
+        b = api.fft_intensity(plan, host, ws=ws)
+        return float((c * torch.nan_to_num(b[4].double(), nan=0.0)).sum().item())
+
+    g = torch.Generator(device="cpu").manual_seed(2048)
+    d = (torch.randn(cell.shape, generator=g) * 0.01 * float(cell.abs().mean())).cuda()
+    fd = (loss(cell + d) - loss(cell - d)) / 2.0
+    an = float((dcell.double() * d.double()).sum().item())
+    assert math.isclose(fd, an, rel_tol=2e-3), (fd, an)

@@ -73,6 +73,29 @@ def test_density_bit_exact(case, dtype):
     assert rng.cpu().tolist() == [lo, hi]
 
 
+@pytest.mark.parametrize("n,kind,dtype", [(96, inputs.SHAPE_SPHERE, "f32"), (128, inputs.SHAPE_CUBE, "f16"),
+                                          (100, inputs.SHAPE_OCTAHEDRON, "f32")])
+def test_rotated_lattice_density_bit_exact_and_fused_forward(n, kind, dtype):
+    """Sec. 2.3 rotated sampling of the cell: ED bit-exact against the float32 oracle (same
+    operation order), and the fused transform of that density against the oracle bins."""
+    w = mof(n, 0.55 * n, kind=kind, rot_seed=3)
+    c = float(n // 2)
+    lat = (inputs.random_rotation(inputs.SplitMix64(11)), (c + 0.37, c - 1.21, c + 2.5))
+    s = w.shape
+    want = density.tile_mask_density(n, w.cell, s.kind, s.center, s.size, s.rot, lattice=lat, out_dtype=dtype)
+    rng = torch.tensor([2 ** 31 - 1, -1], dtype=torch.int32, device="cuda")
+    got = api.build_density(n, dev(w.cell), s, out_dtype=dtype, nz_range=rng, lattice=lat)
+    torch.cuda.synchronize()
+    assert got.cpu().numpy().tobytes() == want.tobytes()
+    lo, hi = density.nonzero_plane_range(want)
+    assert rng.cpu().tolist() == [lo, hi]
+    if dtype == "f32":
+        plan = api.Plan(n, w.dx, w.edges, z0=lo, nz=hi - lo + 1)
+        gb = api.fft_intensity_tiled(plan, dev(w.cell), s, lattice=lat).cpu().numpy()
+        r64 = want.astype(np.float64)
+        compare_bins(gb, oracle_forward(r64, w.dx, w.edges), r64, f"lattice{n}")
+
+
 def test_density_weights_and_plane_subrange():
     w = mof(64, 40)
     weights = np.random.default_rng(3).random((64, 64, 64)).astype(np.float32)
@@ -190,6 +213,25 @@ def test_negative_origin_is_rejected_by_every_entry_point():
         with pytest.raises(api.UrError) as e:
             call()
         assert e.value.status == 1 and "origin" in str(e.value)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    """A device-side wait that nothing completes gives up after its limit (here ~2^24 SM
+    cycles), records the library's error word and returns; ur_sync_status reports
+    UR_ERR_TIMEOUT once, and the next work runs normally."""
+    s = torch.cuda.current_stream()
+    assert api.lib().ur_selftest_wait_timeout(s.cuda_stream) == 0
+    with pytest.raises(api.UrError) as e:
+        api.sync_status()
+    assert e.value.status == 4
+    api.sync_status()   # the word was cleared
+    w = inputs.sc64_workload()
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    got = api.fft_intensity(plan, dev(rho[z0:z0 + nz])).cpu().numpy()
+    r64 = rho.astype(np.float64)
+    compare_bins(got, oracle_forward(r64, w.dx, w.edges), r64, "after timeout")
 
 
 def test_sync_status_after_queued_work():
@@ -517,3 +559,66 @@ def test_large_grid_adjoint_directional_derivative(n, keep_f):
         anm = float((dmask.double() * e.double()).sum().item())
         print(n, "dL/dm", fdm, anm)
         assert math.isclose(fdm, anm, rel_tol=2e-3), (fdm, anm)
+
+
+@pytest.mark.parametrize("n,rot_seed,bw,nl", [(64, None, 0.0, 1), (96, 4, 0.08, 4)])
+def test_ewald_image_matches_oracle(n, rot_seed, bw, nl):
+    """Sec. 2.5 Ewald-sphere extraction from the GPU's half spectrum against the oracle's
+    image of its own FP64 transform.  Gate per pixel: 1e-4 of the largest intensity among
+    the pixel's interpolation corners (FP32 geometry and FP32 spectrum), plus 1e-9 of I(0)."""
+    from oracle import ewald
+    w = mof(n, 0.45 * n, nbins=32)
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
+    H = n // 2 + 1
+    F = torch.empty((n, n, H), dtype=torch.complex64, device="cuda")
+    api.fft_intensity(plan, dev(rho[z0:z0 + nz]), F_out=F)
+    det = {"nx": 61, "ny": 47, "pixel_m": 0.004, "distance_m": 0.3, "beam": (30.0, 20.5), "wavelength_nm": 0.154,
+           "bandwidth": bw, "nlambda": nl,
+           "rot": np.eye(3) if rot_seed is None else inputs.random_rotation(inputs.SplitMix64(rot_seed))}
+    got = api.ewald_image(plan, F, det).cpu().numpy().astype(np.float64)
+    Fo = scatter.dft3(rho.astype(np.float64))
+    want = ewald.ewald_image(Fo, w.dx, det)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    # bound per pixel: the largest corner intensity over its wavelength samples
+    I = scatter.intensity(Fo)
+    kf = ewald.q_samples(det) / scatter.dq_of(n, w.dx)
+    i0 = np.floor(kf).astype(np.int64)
+    cmax = np.zeros(kf.shape[:-1])
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                cmax = np.maximum(cmax, I[(i0[..., 2] + dz) % n, (i0[..., 1] + dy) % n, (i0[..., 0] + dx) % n])
+    bound = 1e-4 * cmax.max(axis=0) + 1e-9 * I[0, 0, 0]
+    ok = np.isfinite(want)
+    assert ok.sum() > 1000
+    assert np.all(np.abs(got[ok] - want[ok]) <= bound[ok])
+
+
+@pytest.mark.parametrize("n,diam", [(512, 240), (256, 110), (128, 60), (96, 44)])
+def test_voxel_sinc_corrected_bins_match_oracle(n, diam):
+    """Sec. 2.5 voxel-sinc correction on every binning path (TMA z pass at 256/512, the
+    power-of-two kernel at 128, the runtime-radix engine at 96, and ur_bin_q) against the
+    oracle's binning of |F|^2 times prod_a sinc^2(pi k_a / N); the adjoint refuses it."""
+    w = mof(n, diam, nbins=128)
+    rho = oracle_density(w)
+    z0, nz = z_range(rho)
+    plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
+    plan.set_voxel_sinc(True)
+    assert plan.voxel_sinc()
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
+    gb = api.fft_intensity(plan, dev(rho[z0:z0 + nz]), ws=ws).cpu().numpy()
+    r64 = rho.astype(np.float64)
+    ob = scatter.forward(r64, w.dx, w.edges, voxel_sinc_correction=True)
+    compare_bins(gb, ob, r64, f"vsinc{n}")
+    if n <= 128:
+        I = torch.from_numpy(np.ascontiguousarray(scatter.intensity(scatter.dft3(r64))[:, :, :n // 2 + 1])
+                             .astype(np.float32)).cuda()
+        compare_bins(api.bin_q(plan, I).cpu().numpy(), ob, r64, f"vsinc bin_q {n}")
+    with pytest.raises(api.UrError) as e:
+        api.backward(plan, torch.zeros(plan.nbins, dtype=torch.float64, device="cuda"), dev(gb), dev(w.cell),
+                     w.shape, ws)
+    assert e.value.status == 5
+    plan.set_voxel_sinc(False)
+    assert not plan.voxel_sinc()
