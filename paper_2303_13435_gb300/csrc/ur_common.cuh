@@ -421,6 +421,59 @@ __device__ __forceinline__ int bin_rank(const int16_t* crs, int shift, const int
 }
 
 // ---------------------------------------------------------------------------
+// Shifted bin sums.  The binning kernels of the power-of-two path sum I - K_j and
+// (I - K_j)^2 per bin, with one shift K_j per bin for the whole call: the first value
+// any block meets in the bin, published once in a 64-bit slot (0 = unset, else
+// (1 << 32) | float bits).  A block keeps the shifts it has seen in shared memory (NaN =
+// not yet fetched).  With K_j a value of the bin, the sums do not cancel when the
+// spread is small, so mean = K + S_d/n and M2 = Q_d - S_d^2/n stay accurate (Chan et
+// al.'s shifted-data form of the variance).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ur_bin_shift(float* Kb, unsigned long long* gK, int b, float v) {
+  float k = Kb[b];
+  if (k != k) {
+    const unsigned long long mine = (1ull << 32) | (unsigned long long)__float_as_uint(v);
+    const unsigned long long old = atomicCAS(gK + b, 0ull, mine);
+    k = old == 0ull ? v : __uint_as_float((unsigned)(old & 0xffffffffull));
+    Kb[b] = k;  // every writer stores the same published value
+  }
+  return k;
+}
+
+// bins field 5 holds the shift slots while the sums accumulate (see ur_bin_shift)
+__host__ __device__ inline unsigned long long* ur_shift_slots(double* bins, int nb) {
+  return reinterpret_cast<unsigned long long*>(bins + UR_BIN_SEM * nb);
+}
+
+// Final statistics of bin j from shifted sums S_d (field 1) and Q_d (field 2) in I' = N^3 I
+// units, the shift slot (field 5) and the plan's count and sum |Q|.
+__device__ __forceinline__ void ur_finalize_shifted(double* __restrict__ bins, const double* __restrict__ geo, int nb,
+                                                    double inv_n3, int j) {
+  const double n = geo[j];
+  const unsigned long long slot = reinterpret_cast<const unsigned long long*>(bins + UR_BIN_SEM * nb)[j];
+  const double K = slot ? (double)__uint_as_float((unsigned)(slot & 0xffffffffull)) : 0.0;
+  const double sd = bins[UR_BIN_SUM_I * nb + j], qd = bins[UR_BIN_SUM_I2 * nb + j];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double mean = nan, sem = nan, sI = 0.0, sI2 = 0.0;
+  if (n > 0) {
+    const double mu = K + sd / n;
+    double m2 = qd - sd * (sd / n);
+    if (m2 < 0) m2 = 0;
+    mean = mu * inv_n3;
+    const double m2i = m2 * (inv_n3 * inv_n3);
+    sI = n * mean;
+    sI2 = m2i + n * mean * mean;
+    if (n > 1) sem = sqrt(m2i / (n * (n - 1.0)));
+  }
+  bins[UR_BIN_COUNT * nb + j] = n;
+  bins[UR_BIN_SUM_I * nb + j] = sI;
+  bins[UR_BIN_SUM_I2 * nb + j] = sI2;
+  bins[UR_BIN_SUM_Q * nb + j] = geo[nb + j];
+  bins[UR_BIN_MEAN * nb + j] = mean;
+  bins[UR_BIN_SEM * nb + j] = sem;
+}
+
+// ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
 struct ur_plan {

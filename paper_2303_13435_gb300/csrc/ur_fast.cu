@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   float* hs2 = hs + a.nbins;
   int16_t* crs = reinterpret_cast<int16_t*>(reinterpret_cast<unsigned char*>(hs) +
                                             ur_align_up_dev((size_t)a.nbins * 8, 16));  // 16-byte aligned
+  float* Kb = reinterpret_cast<float*>(crs);  // forward binning: the block's cache of the bin shifts
   const int c = threadIdx.x % TX, j = threadIdx.x / TX;
   const int col0 = blockIdx.x * TX;
   const int col = col0 + c;
@@ -459,6 +460,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
         hs[i] = 0.f;
         hs2[i] = 0.f;
+        Kb[i] = __int_as_float(0x7fc00000);
       }
       // natural order in shared memory
 #pragma unroll
@@ -469,7 +471,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
         int b = bcur;
         int tnext = b < nb ? thr[b + 1] : 0x7fffffff;
         int s = cc2 + m0 * m0;
-        float sI = 0.f, sI2 = 0.f;
+        // shifted run sums: sum (I - K) and sum (I - K)^2 with the bin's shift K (ur_bin_shift)
+        float sI = 0.f, sI2 = 0.f, K = 0.f;
+        bool fresh = true;
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
           const int mm = m0 + u;
@@ -481,21 +485,29 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
               }
               sI = 0.f;
               sI2 = 0.f;
+              fresh = true;
               do {
                 ++b;
                 tnext = b < nb ? thr[b + 1] : 0x7fffffff;
               } while (s >= tnext);
             }
-            const float sc = a.vs ? csc * __ldg(a.vs + mm) : csc;
-            const float2 f1 = ln[p2pad(mm)];
-            const float i1 = (f1.x * f1.x + f1.y * f1.y) * sc;
-            sI += i1;
-            sI2 += i1 * i1;
-            if (mm != 0 && mm != M) {
-              const float2 f2 = ln[p2pad(N - mm)];
-              const float i2 = (f2.x * f2.x + f2.y * f2.y) * sc;
-              sI += i2;
-              sI2 += i2 * i2;
+            if (b >= 0 && b < nb) {
+              const float sc = a.vs ? csc * __ldg(a.vs + mm) : csc;
+              const float2 f1 = ln[p2pad(mm)];
+              const float i1 = (f1.x * f1.x + f1.y * f1.y) * sc;
+              if (fresh) {
+                K = ur_bin_shift(Kb, a.gK, b, i1);
+                fresh = false;
+              }
+              const float d1 = i1 - K;
+              sI += d1;
+              sI2 = fmaf(d1, d1, sI2);
+              if (mm != 0 && mm != M) {
+                const float2 f2 = ln[p2pad(N - mm)];
+                const float d2 = (f2.x * f2.x + f2.y * f2.y) * sc - K;
+                sI += d2;
+                sI2 = fmaf(d2, d2, sI2);
+              }
             }
             s += 2 * mm + 1;
           }
@@ -686,7 +698,8 @@ template <int N>
 static size_t cols_smem(int nbins, int mode) {
   constexpr int TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2;
   return ur_align_up((size_t)TX * PITCH * sizeof(float2), 16) + ur_align_up((size_t)(nbins + 1) * 4, 16) +
-         ur_align_up((size_t)nbins * 8, 16) + (mode == P2_Z_ADJ ? (size_t)UR_COARSE_ENTRIES * 2 : 0);
+         ur_align_up((size_t)nbins * 8, 16) + (mode == P2_Z_ADJ ? (size_t)UR_COARSE_ENTRIES * 2 : 0) +
+         (mode == P2_Z_BIN ? (size_t)nbins * 4 : 0);
 }
 
 template <int N>

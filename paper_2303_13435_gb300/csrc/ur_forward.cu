@@ -351,6 +351,12 @@ __global__ void k_finalize(double* __restrict__ bins, const double* __restrict__
   finalize_bin(bins, geo, nb, inv_n3, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// finalize of the power-of-two column pass, which leaves shifted sums (ur_bin_shift)
+__global__ void k_finalize_shifted(double* __restrict__ bins, const double* __restrict__ geo, int nb, double inv_n3) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) ur_finalize_shifted(bins, geo, nb, inv_n3, j);
+}
+
 // ---------------------------------------------------------------------------
 // Plan-time bin geometry: count (weighted by the half-spectrum multiplicity)
 // and sum of |Q| per bin over the full N^3 grid; independent of the data.
@@ -698,6 +704,7 @@ ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2
     UR_CUDA_CHECK(cudaMemsetAsync(bins, 0, sizeof(double) * UR_BIN_FIELDS * nb, s));
     a.gsum = bins + UR_BIN_SUM_I * nb;
     a.gsum2 = bins + UR_BIN_SUM_I2 * nb;
+    a.gK = ur_shift_slots(bins, nb);
   } else {
     a.nbins = 0;
   }
@@ -715,7 +722,8 @@ ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2
   ur_timing_end(s);
   if (bins && !zc) {  // (the TMA z-column kernel finalizes the bins itself)
     ur_timing_begin("finalize", s);
-    k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
+    if (p->fast) k_finalize_shifted<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
+    else k_finalize<<<(nb + 255) / 256, 256, 0, s>>>(bins, p->geo, nb, 1.0 / n3);
     UR_LAUNCH_CHECK("k_finalize");
     ur_timing_end(s);
   }

@@ -35,8 +35,10 @@ struct ColArgs {
   int nbins;
   float iscale;      // I' = |F~|^2 * iscale (I' = N^3 I)
   const float* vs;   // voxel-sinc factors sinc^2(pi m / N), m = 0..N/2, or NULL (binning of plain |F|^2)
-  double* gsum;      // [nbins] sum of w I'
-  double* gsum2;     // [nbins] sum of w I'^2
+  double* gsum;      // [nbins] sum of w I' (shifted kernels: of w (I' - K_j))
+  double* gsum2;     // [nbins] sum of w I'^2 (shifted kernels: of w (I' - K_j)^2)
+  unsigned long long* gK;  // shifted kernels: per-bin shift K_j, set once by the first block that
+                           // reaches the bin (0 = unset; else (1 << 32) | float bits)
   float2* fout;      // optional F half spectrum [kz][ky][kx]
   float fscale;
   // adjoint

@@ -60,9 +60,9 @@ struct ZArgs {
   int nbins;
   float iscale;          // I' = |F~|^2 * iscale
   const float* vs;       // voxel-sinc factors sinc^2(pi m / N), m <= N/2, or NULL
-  double* bins;          // [UR_BIN_FIELDS][nbins], zeroed by the caller; during the pass
-                         // field 1 sums n mu, field 2 n mu^2, field 4 the within-block M2
-                         // (I' units) and field 5 slot 0 counts the blocks that are done
+  double* bins;          // [UR_BIN_FIELDS][nbins], zeroed by the caller; during the pass fields
+                         // 1 and 2 hold the shifted sums, field 5 the shifts (ur_bin_shift)
+                         // and field 4 slot 0 counts the blocks that are done
   const double* geo;     // plan: per-bin count and sum |Q|
   double inv_n3;
   float2* fout;          // optional F half spectrum [kz][ky][kx]
@@ -87,7 +87,7 @@ __host__ __device__ inline ZLayout zc_layout(int N, int stage_bytes, int nb) {
   L.thr = o;
   o += zc_align((size_t)(nb + 1) * 4, 16);
   L.acc = o;
-  o += zc_align((size_t)nb * 16, 16);
+  o += zc_align((size_t)nb * 12, 16);
   L.vs = o;
   o += zc_align((size_t)(N / 2 + 1) * 4, 16);
   L.bars = o;
@@ -103,16 +103,6 @@ __device__ __forceinline__ void zc_issue(unsigned char* stage, const CUtensorMap
   for (int k = 0; k < a.nbox; ++k) ur_tma_load_2d(stage + (size_t)k * a.box_rows * 128, tm, T * ZC_TILE, k * a.box_rows, bar);
 }
 
-// per-bin shift of the block: the first value stored wins
-__device__ __forceinline__ float zc_shift(float* Ks, int b, float v) {
-  float k = Ks[b];
-  if (k != k) {
-    const int old = atomicCAS(reinterpret_cast<int*>(Ks + b), (int)ZC_NAN_BITS, __float_as_int(v));
-    k = (old == (int)ZC_NAN_BITS) ? v : __int_as_float(old);
-  }
-  return k;
-}
-
 template <int N>
 __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ CUtensorMap tm, ZArgs a) {
   constexpr int M = N / 2, H = M + 1, A = N / 16, NA = A / 16, CH = (H + 15) / 16;
@@ -125,9 +115,8 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
   float2* xchg = reinterpret_cast<float2*>(sm + L.xchg);
   float2* ztw_s = reinterpret_cast<float2*>(sm + L.ztw);
   int32_t* thr_s = reinterpret_cast<int32_t*>(sm + L.thr);
-  float* Ks = reinterpret_cast<float*>(sm + L.acc);  // per-bin shift, count, shifted sums
-  int* Cs = reinterpret_cast<int*>(Ks + nb);
-  float* Sds = reinterpret_cast<float*>(Cs + nb);
+  float* Kb = reinterpret_cast<float*>(sm + L.acc);  // the block's cache of the bin shifts, shifted sums
+  float* Sds = Kb + nb;
   float* Qds = Sds + nb;
   float* vs_s = reinterpret_cast<float*>(sm + L.vs);    // voxel-sinc factors (when a.vs)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
@@ -139,11 +128,11 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
   if (a.vs)
     for (int i = tid; i <= M; i += ZC_THREADS) vs_s[i] = __ldg(a.vs + i);
   for (int i = tid; i < nb; i += ZC_THREADS) {
-    Ks[i] = __int_as_float((int)ZC_NAN_BITS);
-    Cs[i] = 0;
+    Kb[i] = __int_as_float((int)ZC_NAN_BITS);
     Sds[i] = 0.f;
     Qds[i] = 0.f;
   }
+  unsigned long long* gK = ur_shift_slots(a.bins, nb);
   if (tid == 0) {
     for (int s = 0; s < ZC_STAGES; ++s) ur_mbar_init(bars + s, 1);
     ur_fence_barrier_init();
@@ -240,19 +229,18 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
       // Control flow is warp-uniform (votes): the lanes of a warp walk different chunks, and
       // per-lane branches would split the warp for the rest of the walk.
       const float w = (kx == 0 || kx == M) ? 1.f : 2.f;
-      const int wi = (kx == 0 || kx == M) ? 1 : 2;
       const float csc = a.vs ? a.iscale * (vs_s[kx] * vs_s[ky < 0 ? -ky : ky]) : a.iscale;
       int b = b0;
       int tnext = b < nb ? thr_s[b + 1] : 0x7fffffff;
       int s2 = c2 + m0 * m0;
       float sd = 0.f, sd2 = 0.f;
       int cnt = 0;
-      // shift of the first run: the chunk's first value
+      // shift of the first run (ur_bin_shift: the first value any block meets in the bin)
       float K = 0.f;
       if (b >= 0 && b < nb) {
         const float2 f0 = xw[2 * m0 + cw];
         const float sc0 = a.vs ? csc * vs_s[m0] : csc;
-        K = zc_shift(Ks, b, (f0.x * f0.x + f0.y * f0.y) * sc0);
+        K = ur_bin_shift(Kb, gK, b, (f0.x * f0.x + f0.y * f0.y) * sc0);
       }
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
@@ -266,7 +254,6 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
         bool chg = m <= M && b < nb && s2 >= tnext;
         if (__any_sync(0xffffffffu, chg)) {
           if (chg && cnt > 0) {
-            atomicAdd(Cs + b, wi * cnt);
             atomicAdd(Sds + b, w * sd);
             atomicAdd(Qds + b, w * sd2);
           }
@@ -281,7 +268,7 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
           if (moved) {
             sd = sd2 = 0.f;
             cnt = 0;
-            if (b < nb) K = zc_shift(Ks, b, i1);
+            if (b < nb) K = ur_bin_shift(Kb, gK, b, i1);
           }
         }
         const bool in = m <= M && b >= 0 && b < nb;
@@ -299,7 +286,6 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
         s2 += 2 * m + 1;
       }
       if (cnt > 0 && b >= 0 && b < nb) {
-        atomicAdd(Cs + b, wi * cnt);
         atomicAdd(Sds + b, w * sd);
         atomicAdd(Qds + b, w * sd2);
       }
@@ -309,49 +295,28 @@ __global__ void __launch_bounds__(ZC_THREADS, 2) k_zcol(const __grid_constant__ 
   {
     __syncthreads();
     for (int j = tid; j < nb; j += ZC_THREADS) {
-      const int c = Cs[j];
-      if (c > 0) {
-        const double n = (double)c, K = (double)Ks[j], sd = (double)Sds[j], qd = (double)Qds[j];
-        const double mu = K + sd / n;
-        double m2 = qd - sd * (sd / n);
-        if (m2 < 0.0) m2 = 0.0;
-        atomicAdd(a.bins + UR_BIN_SUM_I * nb + j, n * mu);
-        atomicAdd(a.bins + UR_BIN_SUM_I2 * nb + j, n * mu * mu);
-        atomicAdd(a.bins + UR_BIN_MEAN * nb + j, m2);
-      }
+      if (Sds[j] != 0.f) atomicAdd(a.bins + UR_BIN_SUM_I * nb + j, (double)Sds[j]);
+      if (Qds[j] != 0.f) atomicAdd(a.bins + UR_BIN_SUM_I2 * nb + j, (double)Qds[j]);
     }
-    // the last block to finish turns the sums into the bin statistics: M2 of a bin is the
-    // within-block part plus the between-block part sum n mu^2 - (sum n mu)^2 / n (FP64)
+    // the last block to finish turns the shifted sums into the bin statistics
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
     if (tid == 0)
-      s_last = atomicAdd(reinterpret_cast<unsigned long long*>(a.bins + UR_BIN_SEM * nb), 1ull) ==
+      s_last = atomicAdd(reinterpret_cast<unsigned long long*>(a.bins + UR_BIN_MEAN * nb), 1ull) ==
                (unsigned long long)(gridDim.x - 1);
     __syncthreads();
     if (s_last) {
       __threadfence();
-      const double nan = __longlong_as_double(0x7ff8000000000000ll);
       for (int j = tid; j < nb; j += ZC_THREADS) {
-        const double n = a.geo[j];
-        const double sI = __ldcg(a.bins + UR_BIN_SUM_I * nb + j) * a.inv_n3;
-        const double q = __ldcg(a.bins + UR_BIN_SUM_I2 * nb + j) * (a.inv_n3 * a.inv_n3);
-        const double w2 = __ldcg(a.bins + UR_BIN_MEAN * nb + j) * (a.inv_n3 * a.inv_n3);
-        double mean = nan, sem = nan;
-        if (n > 0) mean = sI / n;
-        if (n > 1) {
-          double between = q - sI * mean;
-          if (between < 0) between = 0;
-          sem = sqrt((w2 + between) / (n * (n - 1.0)));
-        }
-        a.bins[UR_BIN_COUNT * nb + j] = n;
-        a.bins[UR_BIN_SUM_I * nb + j] = sI;
-        a.bins[UR_BIN_SUM_I2 * nb + j] = w2 + q;
-        a.bins[UR_BIN_SUM_Q * nb + j] = a.geo[nb + j];
-        a.bins[UR_BIN_MEAN * nb + j] = mean;
-        // slot 0 of this field held the block counter; every block has read it
-        a.bins[UR_BIN_SEM * nb + j] = sem;
+        // the sums and shifts of the other blocks are in L2
+        a.bins[UR_BIN_SUM_I * nb + j] = __ldcg(a.bins + UR_BIN_SUM_I * nb + j);
+        a.bins[UR_BIN_SUM_I2 * nb + j] = __ldcg(a.bins + UR_BIN_SUM_I2 * nb + j);
+        a.bins[UR_BIN_SEM * nb + j] = __ldcg(a.bins + UR_BIN_SEM * nb + j);
       }
+      __syncthreads();
+      // (slot 0 of the mean field held the block counter; finalize overwrites it)
+      for (int j = tid; j < nb; j += ZC_THREADS) ur_finalize_shifted(a.bins, a.geo, nb, a.inv_n3, j);
     }
   }
 }
