@@ -687,7 +687,15 @@ def run_ooc(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     plan = api.Plan(n, dx, w.edges, z0=z0, nz=P)
-    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_HOST_SLABS)
+    # the out-of-core adjoint's slab of inverse-intermediate planes: as many as about 85 % of
+    # the free device memory holds next to the forward workspace (fewer slabs, fewer rereads)
+    free0 = torch.cuda.mem_get_info()[0]
+    fwd_bytes = plan.workspace_size(api.UR_WS_FORWARD | api.UR_WS_HOST_SLABS)
+    H = n // 2 + 1
+    staging = 2 * 64 * n * n * 4
+    adj_planes = int(max(1, min(n, (0.85 * free0 - fwd_bytes - staging) // (n * H * 8))))
+    plan.set_adj_slab_planes(adj_planes)
+    ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_HOST_SLABS | api.UR_WS_ADJ_SLABS)
     bins = api.new_bins(plan)
     bins_host = torch.empty(bins.shape, dtype=bins.dtype).pin_memory()
 
@@ -709,14 +717,29 @@ def run_ooc(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"out-of-core {n}^3 FP32: 2.6 nm MOF-like cell tiled and cut by a "
                                   f"{64.0 * n / 4096:g} nm sphere, {P} nonzero planes ({moved / 1e9:.1f} GB) in pinned "
-                                  "host memory streamed in double-buffered slabs, 2000 log Q bins, forward only",
+                                  "host memory streamed in double-buffered slabs, 2000 log Q bins; value: the "
+                                  "forward; 'adjoint': the per-slab adjoint (dL/d cell)",
                       "grid": n, "nonzero_planes": P, "slabs": "two device slabs of about 256 MiB (double buffer)"},
            "roofline": {"bound": "h2d", "achieved": achieved, "peak": h2d_peak, "unit": "GB/s",
                         "frac": achieved / h2d_peak, "peak_source": "measured pinned H2D copy of 4 GiB, best of 5",
                         "traffic": None},
            "e2e": {"value": n ** 3 / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(moved),
                    "d2h_bytes_per_step": int(bins_host.numel() * 8)}}
+    # the per-slab adjoint of the same forward (dL/d cell; the z pass recomputed per slab)
+    api.fft_intensity(plan, host, bins=bins, ws=ws)
+    m = bins[4]
+    g = torch.where(torch.isfinite(m) & (m > 0), 1e-3 / torch.nan_to_num(m, nan=1.0).clamp(min=1e-300), 0.0)
+    dcell = torch.empty_like(cell)
+    ms_adj = _timed(lambda: api.backward_slabs(plan, g, bins, cell, w.shape, ws, dl_dcell=dcell), max(1, args.steps // 2),
+                    1)
+    out["adjoint"] = {"ms": ms_adj, "slab_planes": adj_planes, "slabs": -(-n // adj_planes),
+                      "voxels_per_s": n ** 3 / (ms_adj * 1e-3),
+                      "what": "ur_backward_slabs: dL/d cell; per slab the z pass is recomputed from the forward "
+                              "intermediate over every spectrum column, then y inverse and row pass of the slab"}
     if args.check:
+        del ws
+        torch.cuda.empty_cache()
+        ws = plan.workspace(api.UR_WS_FORWARD)
         dev = host.cuda()
         ref = api.fft_intensity(plan, dev, ws=ws).cpu().numpy()
         got = bins_host.numpy()

@@ -119,7 +119,8 @@ enum { UR_WS_FORWARD = 1, UR_WS_BACKWARD = 2, UR_WS_HOST_SLABS = 4, UR_WS_ADJ_SL
  * adds two staging slabs for ED read from pinned host memory.  UR_WS_ADJ_SLABS
  * (ur_backward_slabs) adds, after the forward part and the host staging slabs
  * (counted whether or not UR_WS_HOST_SLABS is given), one slab of the inverse
- * intermediate and two dL/dm staging slabs of ur_plan_set_adj_slab_planes planes. */
+ * intermediate (ur_plan_set_adj_slab_planes planes) and two dL/dm staging
+ * buffers of min(64, that) planes. */
 size_t ur_workspace_size(const ur_plan* plan, int32_t what);
 
 /* Planes per host->device slab of the out-of-core path (default: about
@@ -151,6 +152,17 @@ int32_t ur_plan_chunk_planes(const ur_plan* plan);
  * such plans with UR_ERR_UNSUPPORTED.  ur_plan_voxel_sinc returns 1 when on. */
 ur_status ur_plan_set_voxel_sinc(ur_plan* plan, int32_t on);
 int32_t ur_plan_voxel_sinc(const ur_plan* plan);
+
+/* Engine of the binned z pass for N = 256 and 512 (at most 1024 bins): 0 (the
+ * default) = the compile-time register/shared-memory kernel; 1 = a persistent
+ * kernel that stages 16-column tiles with TMA (cp.async.bulk.tensor, mbarrier
+ * completion, waits bounded to about a second) and transforms each column with
+ * one warp-local exchange.  Both give the same statistics (per-bin shifted sums
+ * merged in FP64); the TMA engine measured slower at 512^3 (its 128 registers
+ * and 111 KB of shared memory per block leave 16 warps per SM).  Other plans get
+ * UR_ERR_UNSUPPORTED for 1.  ur_plan_tma_zpass returns the setting. */
+ur_status ur_plan_set_tma_zpass(ur_plan* plan, int32_t on);
+int32_t ur_plan_tma_zpass(const ur_plan* plan);
 
 /* ---------------------------------------------------------------------------
  * ur_build_density (Sec. 2.3).
@@ -398,9 +410,11 @@ ur_status ur_backward(const ur_plan* plan, const double* dl_dmean, const double*
  * adj_slab_planes output planes the z pass is recomputed over every spectrum
  * column from the forward intermediate in ws (recomputation instead of storing
  * F), and only the slab's planes go through the y inverse and the row pass.
- * dL/du accumulates on the device; dL/dm (optional) is written slab by slab to
- * dl_dmask_host, pinned host float32 [N][N][N], by a copy stream overlapping the
- * next slab (two device staging slabs).  ws: the forward's workspace, sized
+ * dL/du accumulates on the device; dL/dm (optional) is written to
+ * dl_dmask_host, pinned host float32 [N][N][N], in sub-slabs of up to 64 planes
+ * by a copy stream overlapping the next rows (two device staging buffers).
+ * Each slab rereads the whole forward intermediate, so fewer, larger slabs
+ * cost less.  ws: the forward's workspace, sized
  * with UR_WS_FORWARD | UR_WS_ADJ_SLABS, still holding the forward intermediate.
  * Power-of-two grids only (UR_ERR_INVALID otherwise); plans with the voxel-sinc
  * correction get UR_ERR_UNSUPPORTED.  The caller's stream waits for the copies. */

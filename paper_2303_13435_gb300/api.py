@@ -110,6 +110,8 @@ SIGNATURES = {
     "ur_plan_chunk_planes": (_i32, [_vp]),
     "ur_plan_get_tiles": (_i32, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ur_plan_set_voxel_sinc": (_i32, [_vp, _i32]),
+    "ur_plan_set_tma_zpass": (_i32, [_vp, _i32]),
+    "ur_plan_tma_zpass": (_i32, [_vp]),
     "ur_plan_voxel_sinc": (_i32, [_vp]),
 }
 # test hooks (not part of the header's API)
@@ -233,6 +235,13 @@ class Plan:
     def set_voxel_sinc(self, on: bool = True):
         """Bin |F|^2 times the voxel form factor prod_a sinc^2(pi k_a / N) (Sec. 2.5 sinc correction)."""
         _check("ur_plan_set_voxel_sinc", lib().ur_plan_set_voxel_sinc(self._h, 1 if on else 0))
+
+    def set_tma_zpass(self, on: bool = True):
+        """Select the TMA-staged z-pass engine (N = 256, 512) instead of the compile-time kernel."""
+        _check("ur_plan_set_tma_zpass", lib().ur_plan_set_tma_zpass(self._h, 1 if on else 0))
+
+    def tma_zpass(self) -> bool:
+        return bool(lib().ur_plan_tma_zpass(self._h))
 
     def voxel_sinc(self) -> bool:
         return bool(lib().ur_plan_voxel_sinc(self._h))

@@ -461,7 +461,8 @@ extern "C" ur_status ur_backward_slabs(const ur_plan* p, const double* dl_dmean,
   cudaStream_t s = (cudaStream_t)stream;
   const int n = p->n, H = p->H, nb = p->nbins, S = p->adj_slab_planes;
   const double n3 = (double)n * n * n;
-  // workspace: [X][two host staging slabs][Y slab][sigma][two dL/dm staging slabs]
+  // workspace: [X][two host staging slabs][Y slab][sigma][two dL/dm staging slabs of SM planes]
+  const int SM = ur_adj_dm_planes(p);
   float2* X = (float2*)ws;
   char* o = (char*)ws + ur_align_up(p->ws_inter, 256) + 2 * ur_align_up(p->ws_slab, 256);
   float2* Ys = (float2*)o;
@@ -469,7 +470,7 @@ extern "C" ur_status ur_backward_slabs(const ur_plan* p, const double* dl_dmean,
   float* sigma = (float*)o;
   o += ur_align_up(p->ws_sigma, 256);
   float* dm[2];
-  const size_t dm_bytes = (size_t)S * n * n * sizeof(float);
+  const size_t dm_bytes = (size_t)SM * n * n * sizeof(float);
   dm[0] = (float*)o;
   dm[1] = (float*)(o + ur_align_up(dm_bytes, 256));
 
@@ -507,10 +508,9 @@ extern "C" ur_status ur_backward_slabs(const ur_plan* p, const double* dl_dmean,
       st = UR_ERR_CUDA;
     }
   }
-  int slab = 0;
-  for (int za = 0; za < n && st == UR_OK; za += S, ++slab) {
+  int sub = 0;  // running index of the dL/dm staging sub-slabs (double-buffered)
+  for (int za = 0; za < n && st == UR_OK; za += S) {
     const int cnt = za + S <= n ? S : n - za;
-    const int b = slab & 1;
     // z pass over every column, keeping planes [za, za + cnt)
     ColArgs a = ur_col_args(p);
     a.ncols = (long long)n * H;
@@ -547,28 +547,32 @@ extern "C" ur_status ur_backward_slabs(const ur_plan* p, const double* dl_dmean,
     st = ur_fast_cols(n, 1 /* y inverse */, c, s);
     ur_timing_end(s);
     if (st != UR_OK) break;
-    // rows: dL/du accumulated, dL/dm of the slab into staging buffer b
-    if (dl_dmask_host && slab >= 2) cudaStreamWaitEvent(s, freed[b], 0);
-    g.Y = Ys;
-    g.ybase_z = za;
-    g.z0 = za;
-    g.dl_dmask = dl_dmask_host ? dm[b] : nullptr;
-    g.mbase_z = za;
-    ur_timing_begin("adj_rows_grad", s);
-    st = ur_fast_rows_grad(n, g, cnt, s);
-    ur_timing_end(s);
-    if (st != UR_OK) break;
-    if (dl_dmask_host) {
-      cudaEventRecord(done[b], s);
-      cudaStreamWaitEvent(cs, done[b], 0);
-      const cudaError_t ce = cudaMemcpyAsync(dl_dmask_host + (size_t)za * n * n, dm[b], (size_t)cnt * n * n * sizeof(float),
-                                             cudaMemcpyDeviceToHost, cs);
-      if (ce != cudaSuccess) {
-        ur_set_error("ur_backward_slabs: dL/dm copy failed: %s", cudaGetErrorString(ce));
-        st = UR_ERR_CUDA;
-        break;
+    // rows of the slab in sub-slabs of SM planes: dL/du accumulated, dL/dm into staging buffer b
+    for (int zb = za; zb < za + cnt && st == UR_OK; zb += (dl_dmask_host ? SM : cnt), ++sub) {
+      const int cz = dl_dmask_host ? (zb + SM <= za + cnt ? SM : za + cnt - zb) : cnt;
+      const int b = sub & 1;
+      if (dl_dmask_host && sub >= 2) cudaStreamWaitEvent(s, freed[b], 0);
+      g.Y = Ys;
+      g.ybase_z = za;
+      g.z0 = zb;
+      g.dl_dmask = dl_dmask_host ? dm[b] : nullptr;
+      g.mbase_z = zb;
+      ur_timing_begin("adj_rows_grad", s);
+      st = ur_fast_rows_grad(n, g, cz, s);
+      ur_timing_end(s);
+      if (st != UR_OK) break;
+      if (dl_dmask_host) {
+        cudaEventRecord(done[b], s);
+        cudaStreamWaitEvent(cs, done[b], 0);
+        const cudaError_t ce = cudaMemcpyAsync(dl_dmask_host + (size_t)zb * n * n, dm[b], (size_t)cz * n * n * sizeof(float),
+                                               cudaMemcpyDeviceToHost, cs);
+        if (ce != cudaSuccess) {
+          ur_set_error("ur_backward_slabs: dL/dm copy failed: %s", cudaGetErrorString(ce));
+          st = UR_ERR_CUDA;
+          break;
+        }
+        cudaEventRecord(freed[b], cs);
       }
-      cudaEventRecord(freed[b], cs);
     }
   }
   if (cs) {

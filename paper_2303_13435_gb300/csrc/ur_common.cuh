@@ -432,9 +432,14 @@ __device__ __forceinline__ int bin_rank(const int16_t* crs, int shift, const int
 __device__ __forceinline__ float ur_bin_shift(float* Kb, unsigned long long* gK, int b, float v) {
   float k = Kb[b];
   if (k != k) {
-    const unsigned long long mine = (1ull << 32) | (unsigned long long)__float_as_uint(v);
-    const unsigned long long old = atomicCAS(gK + b, 0ull, mine);
-    k = old == 0ull ? v : __uint_as_float((unsigned)(old & 0xffffffffull));
+    // a plain L2 read first: only the first blocks to reach a bin contend on the CAS
+    unsigned long long cur = __ldcg(gK + b);
+    if (cur == 0ull) {
+      const unsigned long long mine = (1ull << 32) | (unsigned long long)__float_as_uint(v);
+      cur = atomicCAS(gK + b, 0ull, mine);
+      if (cur == 0ull) cur = mine;
+    }
+    k = __uint_as_float((unsigned)(cur & 0xffffffffull));
     Kb[b] = k;  // every writer stores the same published value
   }
   return k;
@@ -509,7 +514,8 @@ struct ur_plan {
   int chunk_planes;  // planes per chunk of the plane pass / adjoint y and row passes (n: one launch each)
   size_t ws_chunk;   // adjoint chunk buffer (0 when chunk_planes = n: y-inverse in place)
   float* vsinc;       // device [N/2+1] sinc^2(pi m/N) when the voxel-sinc correction is on, else NULL
-  // TMA z-column kernels (N = 256, 512; NULL otherwise)
+  // TMA z-column kernel (N = 256, 512; NULL otherwise), used when zc_enabled
+  int zc_enabled;
   float2* zc_tw;      // device [N/16][16]: W_N^(t k1)
   int32_t* zc_tiles;  // device: tiles of 16 spectrum columns with a column below the closing threshold
   int zc_ntiles;
@@ -525,3 +531,6 @@ ur_status ur_zcol_forward(const ur_plan* p, const float2* X, double* bins, float
 ur_status ur_deverr_take(void);
 
 static inline size_t ur_align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// planes per dL/dm staging sub-slab of the out-of-core adjoint (at most 64, at most a slab)
+static inline int ur_adj_dm_planes(const ur_plan* p) { return p->adj_slab_planes < 64 ? p->adj_slab_planes : 64; }

@@ -708,8 +708,8 @@ ur_status ur_column_pass(const ur_plan* p, const float2* X, double* bins, float2
   } else {
     a.nbins = 0;
   }
-  // power-of-two grids of 256 and 512 with binning: the TMA z-column kernel
-  const bool zc = bins && p->fast && ur_zcol_supported(p);
+  // grids of 256 and 512 with binning, when the plan asks for it: the TMA z-column kernel
+  const bool zc = bins && p->fast && p->zc_enabled && ur_zcol_supported(p);
   ur_timing_begin("cols_z_bin", s);
   if (zc) {
     UR_TRY(ur_zcol_forward(p, X, bins, F_out, a.iscale, a.fscale, s));

@@ -493,7 +493,7 @@ extern "C" size_t ur_workspace_size(const ur_plan* p, int32_t what) {
     const size_t S = (size_t)p->adj_slab_planes;
     if (!(what & UR_WS_HOST_SLABS)) b += 2 * ur_align_up(p->ws_slab, 256);
     b += ur_align_up(S * p->n * p->H * sizeof(float2), 256) + ur_align_up(p->ws_sigma, 256) +
-         2 * ur_align_up(S * p->n * p->n * sizeof(float), 256);
+         2 * ur_align_up((size_t)ur_adj_dm_planes(p) * p->n * p->n * sizeof(float), 256);
   }
   return b;
 }

@@ -1,6 +1,7 @@
 // Column pass along z (Sec. 2.4 Eq. 2, outer sum) for grid edges N = 256 and
-// 512, fused with |F|^2 and the Sec. 2.5 Q binning, with bin sums formed for a
-// stable standard error.
+// 512, fused with |F|^2 and the Sec. 2.5 Q binning: the TMA-staged engine a
+// plan selects with ur_plan_set_tma_zpass (the default is the compile-time
+// kernel of ur_fast.cu, measured faster at 512^3: 268 against 311 us).
 //
 // Work unit: a tile of 16 consecutive spectrum columns c = ky_index (N/2+1) + kx
 // (the intermediate X[p][ky][kx] seen as rows of N (N/2+1) columns, one row per
@@ -391,6 +392,18 @@ ur_status ur_deverr_take(void) {
 // Host side
 // ---------------------------------------------------------------------------
 bool ur_zcol_supported(const ur_plan* p) { return p->zc_tw != nullptr; }
+
+extern "C" ur_status ur_plan_set_tma_zpass(ur_plan* p, int32_t on) {
+  UR_REQUIRE(p, "ur_plan_set_tma_zpass: null plan");
+  if (on && !ur_zcol_supported(p)) {
+    ur_set_error("ur_plan_set_tma_zpass: the TMA z pass is built for N = 256 and 512 with at most 1024 bins");
+    return UR_ERR_UNSUPPORTED;
+  }
+  p->zc_enabled = on ? 1 : 0;
+  return UR_OK;
+}
+
+extern "C" int32_t ur_plan_tma_zpass(const ur_plan* p) { return (p && p->zc_enabled) ? 1 : 0; }
 
 ur_status ur_zcol_prepare(ur_plan* p) {
   p->zc_tw = nullptr;

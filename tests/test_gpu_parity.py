@@ -325,12 +325,13 @@ def _oracle_counts(n, dx, edges):
     return cnt
 
 
-@pytest.mark.parametrize("n,nbins", [(512, 512), (256, 200), (126, 96), (100, 80)])
-def test_single_voxel_bins_every_voxel_exactly(n, nbins):
+@pytest.mark.parametrize("n,nbins,tma", [(512, 512, False), (512, 512, True), (256, 200, False), (256, 200, True),
+                                         (126, 96, False), (100, 80, False)])
+def test_single_voxel_bins_every_voxel_exactly(n, nbins, tma):
     """The data pass's bin index of every voxel, not the plan's geometry: a unit voxel at the
     origin transforms to F~ = 1 at every k (exactly, in FP32), so the binned sum of I is the
     number of voxels the fused z-pass walk put in each bin.  Power-of-two grids (compile-time
-    kernels) make every term a power of two and the sum exact; the runtime-radix grids carry
+    kernels, and the TMA engine) make every term a power of two and the sum exact; the runtime-radix grids carry
     one FP32 rounding of 1/N^3 per term and at most 1e-6 relative error per bin, below half a
     voxel for these counts."""
     dx = 0.04
@@ -338,6 +339,9 @@ def test_single_voxel_bins_every_voxel_exactly(n, nbins):
     ed = torch.zeros((1, n, n), dtype=torch.float32, device="cuda")
     ed[0, 0, 0] = 1.0
     plan = api.Plan(n, dx, edges, z0=0, nz=1)
+    if tma:
+        plan.set_tma_zpass(True)
+        assert plan.tma_zpass()
     gb = api.fft_intensity(plan, ed).cpu().numpy()
     want = _oracle_counts(n, dx, edges)
     assert np.array_equal(gb[0].astype(np.int64), want)
@@ -488,16 +492,19 @@ def test_backward_fast_path(case):
     assert eu <= GRAD_RTOL and em <= GRAD_RTOL
 
 
-@pytest.mark.parametrize("keep_f", [True, False])
-def test_mof512_full_size_forward_and_adjoint(keep_f):
+@pytest.mark.parametrize("keep_f,tma", [(True, False), (False, False), (False, True)])
+def test_mof512_full_size_forward_and_adjoint(keep_f, tma):
     """The 512^3 workload of the benchmark against the FP64 oracle: fused tiled forward,
-    then the adjoint from the kept half spectrum F (the benchmark's launch configuration)
-    or recomputing F along z from the plane-pass intermediate."""
+    then the adjoint from the kept half spectrum F or recomputing F along z from the
+    plane-pass intermediate (the benchmark's launch configuration); the forward on both
+    z-pass engines."""
     w = inputs.mof_workload(n=512, diameter_nm=10.0, nbins=512)
     rho = oracle_density(w)
     z0, nz = z_range(rho)
     assert nz == 247
     plan = api.Plan(w.n, w.dx, w.edges, z0=z0, nz=nz)
+    if tma:
+        plan.set_tma_zpass(True)
     ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
     Fh = torch.empty((512, 512, 257, 2), device="cuda") if keep_f else None
     bins = api.fft_intensity_tiled(plan, dev(w.cell), w.shape, ws=ws, F_out=Fh)
@@ -596,10 +603,11 @@ def test_ewald_image_matches_oracle(n, rot_seed, bw, nl):
     assert np.all(np.abs(got[ok] - want[ok]) <= bound[ok])
 
 
-@pytest.mark.parametrize("n,diam", [(512, 240), (256, 110), (128, 60), (96, 44)])
-def test_voxel_sinc_corrected_bins_match_oracle(n, diam):
-    """Sec. 2.5 voxel-sinc correction on every binning path (TMA z pass at 256/512, the
-    power-of-two kernel at 128, the runtime-radix engine at 96, and ur_bin_q) against the
+@pytest.mark.parametrize("n,diam,tma", [(512, 240, False), (512, 240, True), (256, 110, False), (256, 110, True),
+                                        (128, 60, False), (96, 44, False)])
+def test_voxel_sinc_corrected_bins_match_oracle(n, diam, tma):
+    """Sec. 2.5 voxel-sinc correction on every binning path (both z-pass engines at 256/512,
+    the power-of-two kernel at 128, the runtime-radix engine at 96, and ur_bin_q) against the
     oracle's binning of |F|^2 times prod_a sinc^2(pi k_a / N); the adjoint refuses it."""
     w = mof(n, diam, nbins=128)
     rho = oracle_density(w)
@@ -607,6 +615,8 @@ def test_voxel_sinc_corrected_bins_match_oracle(n, diam):
     plan = api.Plan(n, w.dx, w.edges, z0=z0, nz=nz)
     plan.set_voxel_sinc(True)
     assert plan.voxel_sinc()
+    if tma:
+        plan.set_tma_zpass(True)
     ws = plan.workspace(api.UR_WS_FORWARD | api.UR_WS_BACKWARD)
     gb = api.fft_intensity(plan, dev(rho[z0:z0 + nz]), ws=ws).cpu().numpy()
     r64 = rho.astype(np.float64)
