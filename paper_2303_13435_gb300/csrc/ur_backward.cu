@@ -60,7 +60,7 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
   if (r0 >= nrows) return;  // uniform over the block
   for (int i = threadIdx.x; i < U; i += blockDim.x) acc[i] = 0.f;
   const float* crow = cell + ((long long)cz * U + cy) * U;
-  const FastDiv dM((uint32_t)M), dH((uint32_t)H), dNy((uint32_t)(nyr > 0 ? nyr : 1));
+  const FastDiv dM((uint32_t)M), dH((uint32_t)H), dNy((uint32_t)(nyr > 0 ? nyr : 1)), dU((uint32_t)U);
   __syncthreads();
   {
     const int nb = min(RB, nrows - r0);
@@ -81,8 +81,9 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
     __syncthreads();
     // Hermitian half -> packed complex sequence, in place by (k, M-k) pairs
     const int half = M / 2 + 1;
+    const FastDiv dhalf((uint32_t)half);
     for (int f = threadIdx.x; f < RB * half; f += blockDim.x) {
-      const int t = f / half;
+      const int t = (int)dhalf.div((uint32_t)f);
       const int k = f - t * half;
       float2* X = buf + t * H;
       const float2 xa = X[k], xb = X[M - k];
@@ -115,7 +116,7 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
       const float2 zv = buf[t * H + m];
       const float g0 = zv.x * inv_n3, g1 = zv.y * inv_n3;
       const int x0 = 2 * m;
-      const int c0 = (x0 + ox) % U, c1 = (x0 + 1 + ox) % U;
+      const int c0 = (int)dU.mod((uint32_t)(x0 + ox)), c1 = (int)dU.mod((uint32_t)(x0 + 1 + ox));
       const long long vox = ((long long)z * N + y) * N + x0;
       if (dl_dmask) {
         const float u0 = __ldg(crow + c0), u1 = __ldg(crow + c1);

@@ -357,24 +357,10 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ buf, int pitch, i
 // the order 8, 4, 2, 3, 5, 7): a single loop with a switch over the radix
 // makes the compiler keep the register arrays of every case live at once.
 template <int R, bool INV, int EMAX>
-__device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, const StageInfo* __restrict__ st,
-                                             int nst, const float2* __restrict__ tw, int i) {
+__device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, const StageInfo* st, int nst,
+                                             const float2* __restrict__ tw, int i) {
   while (i < nst) {
-    StageInfo si;
-    {
-      // volatile: keep the per-stage loads inside the caller's loops
-      const volatile StageInfo* vs = st + i;
-      si.R = vs->R;
-      si.nb = vs->nb;
-      si.Ns = vs->Ns;
-      si.tstep = vs->tstep;
-      si.div_nb.d = vs->div_nb.d;
-      si.div_nb.m = vs->div_nb.m;
-      si.div_nb.s = vs->div_nb.s;
-      si.div_ns.d = vs->div_ns.d;
-      si.div_ns.m = vs->div_ns.m;
-      si.div_ns.s = vs->div_ns.s;
-    }
+    const StageInfo si = st[i];  // shared memory (fft_lines): a broadcast read per stage
     if (si.R != R) break;
     fft_stage<R, INV, EMAX>(buf, pitch, lines, si, tw);
     ++i;
@@ -382,16 +368,28 @@ __device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, 
   return i;
 }
 
+// The schedule is copied to shared memory once per call: reading it from
+// global memory at every stage put an L2 round trip in front of each stage.
 template <bool INV, int EMAX>
 __device__ __forceinline__ void fft_lines(float2* buf, int pitch, int lines, const StageInfo* __restrict__ st, int nst,
                           const float2* __restrict__ tw) {
+  static_assert(sizeof(StageInfo) % 4 == 0, "StageInfo is copied as 32-bit words");
+  constexpr int W = (int)(sizeof(StageInfo) / 4);
+  __shared__ __align__(16) uint32_t s_raw[UR_MAX_STAGES * W];  // raw words: StageInfo has constructors
+  const StageInfo* s_st = reinterpret_cast<const StageInfo*>(s_raw);
+  __syncthreads();  // an earlier call of this kernel may still read s_raw
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(st);
+    for (int w = threadIdx.x; w < nst * W; w += blockDim.x) s_raw[w] = __ldg(src + w);
+  }
+  __syncthreads();
   int i = 0;
-  i = fft_stages_of<8, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
-  i = fft_stages_of<4, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
-  i = fft_stages_of<2, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
-  i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
-  i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
-  i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, st, nst, tw, i);
+  i = fft_stages_of<8, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<4, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<2, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
 }
 
 // ---------------------------------------------------------------------------

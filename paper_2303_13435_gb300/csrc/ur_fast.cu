@@ -460,7 +460,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       for (int i = s_blo + (int)threadIdx.x; i <= s_bhi; i += blockDim.x) {
         hs[i] = 0.f;
         hs2[i] = 0.f;
-        Kb[i] = __int_as_float(0x7fc00000);
+        // the shifts already published for the block's bins, fetched together up front (a
+        // fetch inside the walk would stall it); unset ones are NaN and published on first use
+        const unsigned long long g = __ldcg(a.gK + i);
+        Kb[i] = g ? __uint_as_float((unsigned)(g & 0xffffffffull)) : __int_as_float(0x7fc00000);
       }
       // natural order in shared memory
 #pragma unroll

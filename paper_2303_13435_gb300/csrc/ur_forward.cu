@@ -55,6 +55,8 @@ __device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, 
   const int M = N >> 1, H = M + 1;
   const long long r0 = blk * RB;
   const FastDiv dm((uint32_t)M), dh((uint32_t)H);
+  // generated rows: row r = p N + y (r < 2^31) and the cell indices, by multiply-shift
+  const FastDiv dn((uint32_t)N), du((uint32_t)(GEN ? ra.ucell : 1));
   for (int f = threadIdx.x; f < RB * M; f += blockDim.x) {
     const int t = (int)dm.div((uint32_t)f);
     const int m = f - t * M;
@@ -62,8 +64,9 @@ __device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, 
     float2 v = make_float2(0.f, 0.f);
     if (r < nrows) {
       if (GEN) {
-        const int p = (int)(r / N), y = (int)(r - (long long)p * N), z = ra.z0 + p, x = 2 * m, U = ra.ucell;
-        const float* crow = ra.cell + ((long long)((z + ra.oz) % U) * U + (y + ra.oy) % U) * U;
+        const int p = (int)dn.div((uint32_t)r), y = (int)r - p * N, z = ra.z0 + p, x = 2 * m, U = ra.ucell;
+        const float* crow =
+            ra.cell + ((long long)du.mod((uint32_t)(z + ra.oz)) * U + du.mod((uint32_t)(y + ra.oy))) * U;
         float m0, m1;
         if (ra.weights) {
           const float2 mw = __ldg(reinterpret_cast<const float2*>(ra.weights + ((long long)z * N + y) * N + x));
@@ -77,7 +80,8 @@ __device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, 
           v = make_float2(__fmul_rn(lattice_sample(ra.lat, ra.sh, ra.cell, U, x, y, z), m0),
                           __fmul_rn(lattice_sample(ra.lat, ra.sh, ra.cell, U, x + 1, y, z), m1));
         else
-          v = make_float2(__fmul_rn(__ldg(crow + (x + ra.ox) % U), m0), __fmul_rn(__ldg(crow + (x + 1 + ra.ox) % U), m1));
+          v = make_float2(__fmul_rn(__ldg(crow + du.mod((uint32_t)(x + ra.ox))), m0),
+                          __fmul_rn(__ldg(crow + du.mod((uint32_t)(x + 1 + ra.ox))), m1));
       } else {
         v = load_pair<T>(ed + r * N + 2 * m);
       }
@@ -113,34 +117,42 @@ __global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, 
 // has elements src[(c / H) * A + c % H + i * S], i < nload, placed at shared
 // position zoff + i (all other positions zero).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long col_offset(long long c, int H, long long A) {
-  const long long o = c / H;
-  return o * A + (c - o * H);
+// Column indices stay below 2^31 (at most N (N/2+1) columns), so the block's
+// index arithmetic runs in 32 bits with multiply-shift division (FastDiv).
+struct ColDivs {
+  FastDiv tx, h;
+  __device__ explicit ColDivs(const ColArgs& a) : tx((uint32_t)a.TX), h((uint32_t)a.H) {}
+};
+
+__device__ __forceinline__ long long col_offset(uint32_t c, const FastDiv& dh, long long A) {
+  const uint32_t o = dh.div(c);
+  return (long long)o * A + (c - o * dh.d);
 }
 
-__device__ __forceinline__ void load_columns(const ColArgs& a, float2* buf, long long c0, int N) {
+__device__ __forceinline__ void load_columns(const ColArgs& a, const ColDivs& dv, float2* buf, long long c0, int N) {
   const int TX = a.TX;
   for (int f = threadIdx.x; f < TX * N; f += blockDim.x) {
-    const int i = f / TX;
+    const int i = (int)dv.tx.div((uint32_t)f);
     const int t = f - i * TX;
     const long long c = c0 + t;
     const int li = i - a.zoff;
     float2 v = make_float2(0.f, 0.f);
     if (c < a.ncols && li >= 0 && li < a.nload) {
-      v = __ldg(a.src + col_offset(c, a.H, a.A) + (long long)li * a.S);
+      v = __ldg(a.src + col_offset((uint32_t)c, dv.h, a.A) + (long long)li * a.S);
     }
     buf[t * a.pitch + i] = v;
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ void store_columns(const ColArgs& a, const float2* buf, long long c0, int N) {
+__device__ __forceinline__ void store_columns(const ColArgs& a, const ColDivs& dv, const float2* buf, long long c0,
+                                              int N) {
   const int TX = a.TX;
   for (int f = threadIdx.x; f < TX * N; f += blockDim.x) {
-    const int i = f / TX;
+    const int i = (int)dv.tx.div((uint32_t)f);
     const int t = f - i * TX;
     const long long c = c0 + t;
-    if (c < a.ncols) a.dst[col_offset(c, a.H, a.Ad) + (long long)i * a.Sd] = buf[t * a.pitch + i];
+    if (c < a.ncols) a.dst[col_offset((uint32_t)c, dv.h, a.Ad) + (long long)i * a.Sd] = buf[t * a.pitch + i];
   }
 }
 
@@ -149,17 +161,19 @@ __device__ __forceinline__ void store_columns(const ColArgs& a, const float2* bu
 // bin index only moves forward inside a chunk.  kz = m and kz = N - m share k^2.
 // Op(t, m, bin, weight) is called for every pair.
 template <typename Op>
-__device__ __forceinline__ void walk_bins(const ColArgs& a, const int32_t* __restrict__ thr, long long c0, Op op) {
+__device__ __forceinline__ void walk_bins(const ColArgs& a, const ColDivs& dv, const int32_t* __restrict__ thr,
+                                          long long c0, Op op) {
   const int M = a.M, H = a.H, N = a.N;
   const int nch = (H + BIN_CHUNK - 1) / BIN_CHUNK;
   const int ntask = a.TX * nch;
+  const FastDiv dch((uint32_t)nch);
   for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-    const int t = task / nch;
+    const int t = (int)dch.div((uint32_t)task);
     const int ch = task - t * nch;
     const long long c = c0 + t;
     if (c >= a.ncols) continue;
-    const int kyi = (int)(c / H);
-    const int kx = (int)(c - (long long)kyi * H);
+    const int kyi = (int)dv.h.div((uint32_t)c);
+    const int kx = (int)c - kyi * H;
     const int ky = kyi < M ? kyi : kyi - N;
     const int c2 = kx * kx + ky * ky;
     const float w = (kx == 0 || kx == M) ? 1.f : 2.f;
@@ -250,6 +264,7 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
   double* hs = nullptr;
   double* hs2 = nullptr;
   const long long c0 = blk * a.TX;
+  const ColDivs dv(a);
   if (MODE != COL_Y && a.nbins > 0) {
     for (int j = threadIdx.x; j <= a.nbins; j += blockDim.x) thr[j] = __ldg(a.thr + j);
     if (MODE == COL_ZBIN) {
@@ -266,8 +281,8 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
     // bins this tile can reach: k^2 in [min kx^2+ky^2, max kx^2+ky^2 + (N/2)^2]
     if (threadIdx.x < a.TX && c0 + threadIdx.x < a.ncols) {
       const long long c = c0 + threadIdx.x;
-      const int kyi = (int)(c / a.H);
-      const int kx = (int)(c - (long long)kyi * a.H);
+      const int kyi = (int)dv.h.div((uint32_t)c);
+      const int kx = (int)c - kyi * a.H;
       const int ky = kyi < a.M ? kyi : kyi - N;
       const int c2 = kx * kx + ky * ky;
       atomicMin(&s_blo, max(bin_search(thr, a.nbins, c2), 0));
@@ -280,15 +295,15 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
     }
   }
   {
-    load_columns(a, buf, c0, N);
+    load_columns(a, dv, buf, c0, N);
     if (MODE == COL_Y) {
       fft_lines<INV, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
-      store_columns(a, buf, c0, N);
+      store_columns(a, dv, buf, c0, N);
     } else if (MODE == COL_ZBIN) {
       fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
       if (a.fout) {
         for (int f = threadIdx.x; f < a.TX * N; f += blockDim.x) {
-          const int i = f / a.TX;
+          const int i = (int)dv.tx.div((uint32_t)f);
           const int t = f - i * a.TX;
           const long long c = c0 + t;
           if (c < a.ncols) a.fout[(long long)i * N * a.H + c] = cscale(buf[t * a.pitch + i], a.fscale);
@@ -296,15 +311,15 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
       }
       if (a.nbins > 0) {
         BinAccum acc{buf, a.pitch, a.M, N, a.nbins, a.iscale, hs, hs2, -1, 0.f, 0.f, a.vs, 1.f};
-        walk_bins(a, thr, c0, acc);
+        walk_bins(a, dv, thr, c0, acc);
       }
     } else {  // COL_ZADJ: F along z (recomputed or given), times sigma(bin), inverse along z
       if (!a.skip_fwd) fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
       SigmaScale sc{buf, a.pitch, a.M, N, a.nbins, a.sigma};
-      walk_bins(a, thr, c0, sc);
+      walk_bins(a, dv, thr, c0, sc);
       __syncthreads();
       fft_lines<true, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
-      store_columns(a, buf, c0, N);
+      store_columns(a, dv, buf, c0, N);
     }
   }
   if (MODE == COL_ZBIN && a.nbins > 0) {
