@@ -73,6 +73,43 @@ def test_batch_matches_single_instance_and_oracle():
         assert normwise(batch.dl_dcell[i].cpu().numpy(), gu) <= GRAD_RTOL
 
 
+def test_batch_at_large_smooth_edges_matches_oracle():
+    """Edges 250 = 2 5^3, 270 = 2 3^3 5 and 378 = 2 3^3 7 (radix-5 and radix-7 stages, runtime
+    schedules) in one batch: bins against the FP64 oracle, and dL/du of the 250 particle against
+    the oracle's gradient."""
+    cell_np = inputs.mof_like_cell(64, 2.6, 0)
+    cell = torch.from_numpy(cell_np).cuda()
+    rot = inputs.random_rotation(inputs.SplitMix64(11))
+    parts = [inputs.Particle(250, inputs.Shape(inputs.SHAPE_SPHERE, (125.0, 125.0, 125.0), 60.0)),
+             inputs.Particle(270, inputs.Shape(inputs.SHAPE_CUBE, (135.0, 135.0, 135.0), 40.0, rot)),
+             inputs.Particle(378, inputs.Shape(inputs.SHAPE_OCTAHEDRON, (189.0, 189.0, 189.0), 90.0, rot))]
+    edges = inputs.log_edges(2 * math.pi / (378 * DX), math.pi / DX, 96)
+    plans, rhos = [], []
+    for p in parts:
+        rho = density.tile_mask_density(p.n, cell_np, p.shape.kind, p.shape.center, p.shape.size, p.shape.rot)
+        nzp = np.flatnonzero(rho.any(axis=(1, 2)))
+        plans.append(api.Plan(p.n, DX, edges, z0=int(nzp[0]), nz=int(nzp[-1] - nzp[0] + 1)))
+        rhos.append(rho)
+    batch = api.Batch(plans, cell, [p.shape for p in parts])
+    batch.forward()
+    torch.cuda.synchronize()
+    obs = []
+    for i, p in enumerate(parts):
+        r64 = rhos[i].astype(np.float64)
+        ob = oracle_forward(r64, DX, edges)
+        print(p.n, compare_bins(batch.bins[i].cpu().numpy(), ob, r64, f"batch edge {p.n}"))
+        obs.append(ob)
+    for i in range(len(parts)):
+        batch.dl_dmean[i].copy_(torch.from_numpy(_g(batch.bins[i].cpu().numpy())).cuda())
+    batch.backward()
+    torch.cuda.synchronize()
+    p = parts[0]
+    mask = density.mask_values(p.n, p.shape.kind, p.shape.center, p.shape.size, p.shape.rot)
+    gu, _ = oracle_grads(rhos[0].astype(np.float64), cell_np.astype(np.float64), mask, DX, edges,
+                         batch.dl_dmean[0].cpu().numpy(), obs[0]["count"])
+    assert normwise(batch.dl_dcell[0].cpu().numpy(), gu) <= GRAD_RTOL
+
+
 def test_batch_in_one_cuda_graph():
     parts, plans, _, cell, _, _ = _setup(count=4, seed=11)
     batch = api.Batch(plans, cell, [p.shape for p in parts])

@@ -131,7 +131,8 @@ def gpu_forward(w, rho, F=False, dtype="f32"):
     return plan, bins.cpu().numpy(), (Fo.cpu().numpy() if F else None)
 
 
-@pytest.mark.parametrize("case", ["sc64", "mof96", "mof98", "mof100", "mof120_cube", "mof128_small", "mof160"])
+@pytest.mark.parametrize("case", ["sc64", "mof96", "mof98", "mof100", "mof120_cube", "mof128_small", "mof160",
+                                  "mof250", "mof270", "mof378"])
 def test_forward_bins_match_oracle(case):
     if case == "sc64":
         w = inputs.sc64_workload()
