@@ -140,7 +140,7 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
     if (acc[i] != 0.f) atomicAdd(dl_dcell + ((long long)cz * U + cy) * U + i, acc[i]);
 }
 
-__global__ void __launch_bounds__(256, 2) k_rows_grad(GenGradArgs g) { rows_grad_body(g, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(256, 4) k_rows_grad(GenGradArgs g) { rows_grad_body(g, blockIdx.x, blockIdx.y); }
 
 // Log-I(Q) MSE and its gradient: one thread per bin over blocks of 64 threads
 // (the float64 logarithms are the cost, so they are spread over many SMs).
@@ -386,7 +386,7 @@ __global__ void k_batch_sigma(const BatchSigmaItem* __restrict__ items) {
   it.sigma[j] = (float)(n > 0 ? 2.0 * it.g[j] / n / it.n3 : 0.0);
 }
 
-__global__ void __launch_bounds__(256, 2) k_batch_grad(const BatchGradItem* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_batch_grad(const BatchGradItem* __restrict__ items,
                                                        const long long* __restrict__ start, int count) {
   int lo = 0, hi = count - 1;
   const long long b = blockIdx.x;

@@ -236,6 +236,39 @@ UR_HD constexpr float ur_cos32(int m) {
 UR_HD constexpr float ur_w32_re(int m) { return ur_cos32(m); }
 UR_HD constexpr float ur_w32_im(int m) { return -ur_cos32(m - 8); }  // -sin(2 pi m / 32)
 
+// exp(-2 pi i m / L), m < L, for the inner twiddles of composite radices L that
+// do not divide 32: cos and sin from their Taylor series, summed in double at
+// compile time on the argument reduced to [-pi, pi], then rounded to float.
+UR_HD constexpr double ur_ct_sin(double x) {
+  double t = x, s = x;
+  for (int k = 1; k < 30; ++k) {
+    t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    s += t;
+  }
+  return s;
+}
+UR_HD constexpr double ur_ct_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    s += t;
+  }
+  return s;
+}
+template <int L>
+struct UrTw {
+  float re[L], im[L];
+  UR_HD constexpr UrTw() : re(), im() {
+    constexpr double pi = 3.14159265358979323846;
+    for (int m = 0; m < L; ++m) {
+      double x = 2.0 * pi * (double)m / (double)L;
+      if (x > pi) x -= 2.0 * pi;
+      re[m] = (float)ur_ct_cos(x);
+      im[m] = (float)(-ur_ct_sin(x));
+    }
+  }
+};
+
 // L = R1 R2 point DFT from R1- and R2-point DFTs (n = R2 n1 + n2, k = k1 + R1 k2):
 //   X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) [W_L^(n2 k1) sum_n1 a[R2 n1 + n2] W_R1^(n1 k1)]
 template <int R, bool INV>
@@ -253,8 +286,14 @@ UR_HD __forceinline__ void dft_split(float2* a) {
     dft<R1, INV>(t);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
-      const int m = (n2 * k1 * (32 / L)) & 31;
-      y[n2 * R1 + k1] = (n2 * k1 == 0) ? t[k1] : twmul<INV>(t[k1], make_float2(ur_w32_re(m), ur_w32_im(m)));
+      if constexpr (32 % L == 0) {
+        const int m = (n2 * k1 * (32 / L)) & 31;
+        y[n2 * R1 + k1] = (n2 * k1 == 0) ? t[k1] : twmul<INV>(t[k1], make_float2(ur_w32_re(m), ur_w32_im(m)));
+      } else {
+        constexpr UrTw<L> W{};
+        const int m = (n2 * k1) % L;
+        y[n2 * R1 + k1] = (n2 * k1 == 0) ? t[k1] : twmul<INV>(t[k1], make_float2(W.re[m], W.im[m]));
+      }
     }
   }
 #pragma unroll
@@ -280,6 +319,12 @@ UR_HD __forceinline__ void dft(float2* a) {
     dft_split<4, 4, INV>(a);
   } else if constexpr (R == 32) {
     dft_split<4, 8, INV>(a);
+  } else if constexpr (R == 6) {
+    dft_split<2, 3, INV>(a);
+  } else if constexpr (R == 9) {
+    dft_split<3, 3, INV>(a);
+  } else if constexpr (R == 10) {
+    dft_split<2, 5, INV>(a);
   } else {
     dft_odd<R, INV>(a);
   }
@@ -292,6 +337,11 @@ UR_HD __forceinline__ void dft(float2* a) {
 // radices of the earlier stages.
 // ---------------------------------------------------------------------------
 #define UR_MAX_STAGES 14
+// Radices of the shared-memory engine, in the order their stages run (each radix
+// has its own loop in fft_lines; a schedule lists its stages in this order).
+// (Composites of 12 and more points spilled registers at 64 per thread.)
+#define UR_NRADIX 9
+static constexpr int ur_radix_order[UR_NRADIX] = {8, 4, 2, 6, 10, 9, 3, 5, 7};
 struct StageInfo {
   int R, nb, Ns, tstep;  // tstep = n_tab / (Ns * R)
   FastDiv div_nb, div_ns;
@@ -354,7 +404,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ buf, int pitch, i
 // stage table `st` (nst stages, device memory).  Requires lines * L <= EMAX *
 // blockDim.x.  Every thread of the block must call it.
 // The stages of one radix run in their own loop (schedules list radices in
-// the order 8, 4, 2, 3, 5, 7): a single loop with a switch over the radix
+// the order of ur_radix_order): a single loop with a switch over the radix
 // makes the compiler keep the register arrays of every case live at once.
 template <int R, bool INV, int EMAX>
 __device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, const StageInfo* st, int nst,
@@ -387,6 +437,9 @@ __device__ __forceinline__ void fft_lines(float2* buf, int pitch, int lines, con
   i = fft_stages_of<8, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<4, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<2, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<6, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<10, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+  i = fft_stages_of<9, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);

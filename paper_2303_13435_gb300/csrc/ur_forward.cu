@@ -107,7 +107,7 @@ __device__ __forceinline__ void rows_r2c_body(const RowArgs& ra, int N, int RB, 
 }
 
 template <int GEN, typename T>
-__global__ void __launch_bounds__(256, 2) k_rows_r2c(RowArgs ra, int N, int RB, const StageInfo* __restrict__ sched,
+__global__ void __launch_bounds__(256, 4) k_rows_r2c(RowArgs ra, int N, int RB, const StageInfo* __restrict__ sched,
                                                      int nst) {
   rows_r2c_body<GEN, T>(ra, N, RB, sched, nst, blockIdx.x);
 }
@@ -332,7 +332,7 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
 }
 
 template <int MODE, bool INV>
-__global__ void __launch_bounds__(256, 2) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(256, 4) k_cols(ColArgs a) {
   cols_body<MODE, INV>(a, blockIdx.x);
 }
 
@@ -840,7 +840,7 @@ __device__ __forceinline__ int batch_item(const long long* __restrict__ start, i
   return lo;
 }
 
-__global__ void __launch_bounds__(256, 2) k_batch_rows(const BatchRowsItem* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_batch_rows(const BatchRowsItem* __restrict__ items,
                                                        const long long* __restrict__ start, int count) {
   const int i = batch_item(start, count, blockIdx.x);
   const BatchRowsItem& it = items[i];
@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_rows(const BatchRowsItem* __re
 }
 
 template <int MODE, bool INV>
-__global__ void __launch_bounds__(256, 2) k_batch_cols(const ColArgs* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_batch_cols(const ColArgs* __restrict__ items,
                                                        const long long* __restrict__ start, int count) {
   const int i = batch_item(start, count, blockIdx.x);
   cols_body<MODE, INV>(items[i], blockIdx.x - __ldg(start + i));

@@ -139,16 +139,38 @@ extern "C" int32_t ur_last_timings(float* ms_out, int32_t max_entries, const cha
 bool ur_make_sched(int L, int n_tab, Sched* out) {
   memset(out, 0, sizeof *out);
   out->L = L;
+  // prime exponents, then few stages from the kernels' radices: 8s, a leftover 2
+  // merged with a 3 or a 5 (6, 10), pairs of 3s as 9.  Fewer stages mean fewer
+  // shared-memory round trips.
+  int e2 = 0, e3 = 0, e5 = 0, e7 = 0;
+  int r = L;
+  while (r % 2 == 0) { ++e2; r /= 2; }
+  while (r % 3 == 0) { ++e3; r /= 3; }
+  while (r % 5 == 0) { ++e5; r /= 5; }
+  while (r % 7 == 0) { ++e7; r /= 7; }
+  if (r != 1 || L < 1 || n_tab % L != 0) return false;
+  int cnt[UR_NRADIX] = {0};  // per entry of ur_radix_order
+  auto add = [&](int R) {
+    for (int i = 0; i < UR_NRADIX; ++i)
+      if (ur_radix_order[i] == R) ++cnt[i];
+  };
+  for (; e2 >= 3; e2 -= 3) add(8);
+  if (e2 == 2) {
+    add(4);
+  } else if (e2 == 1) {
+    if (e3 > 0) { add(6); --e3; }
+    else if (e5 > 0) { add(10); --e5; }
+    else add(2);
+  }
+  for (; e3 >= 2; e3 -= 2) add(9);
+  if (e3 == 1) add(3);
+  for (; e5 > 0; --e5) add(5);
+  for (; e7 > 0; --e7) add(7);
   int rad[64];
   int nr = 0;
-  int r = L;
-  while (r % 8 == 0) { rad[nr++] = 8; r /= 8; }
-  while (r % 4 == 0) { rad[nr++] = 4; r /= 4; }
-  while (r % 2 == 0) { rad[nr++] = 2; r /= 2; }
-  while (r % 3 == 0) { rad[nr++] = 3; r /= 3; }
-  while (r % 5 == 0) { rad[nr++] = 5; r /= 5; }
-  while (r % 7 == 0) { rad[nr++] = 7; r /= 7; }
-  if (r != 1 || nr > UR_MAX_STAGES || n_tab % L != 0) return false;
+  for (int i = 0; i < UR_NRADIX; ++i)
+    for (int c = 0; c < cnt[i]; ++c) rad[nr++] = ur_radix_order[i];
+  if (nr > UR_MAX_STAGES) return false;
   int Ns = 1;
   for (int i = 0; i < nr; ++i) {
     StageInfo& si = out->st[i];
@@ -260,6 +282,9 @@ extern "C" double ur_selftest_dft(void) {
   e = fmax(e, dft_err_both<8>(st));
   e = fmax(e, dft_err_both<16>(st));
   e = fmax(e, dft_err_both<32>(st));
+  e = fmax(e, dft_err_both<6>(st));
+  e = fmax(e, dft_err_both<9>(st));
+  e = fmax(e, dft_err_both<10>(st));
   return e;
 }
 
