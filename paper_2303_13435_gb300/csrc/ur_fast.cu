@@ -301,7 +301,7 @@ template <int N, int MODE = P2_Y_FWD>
 struct ColCfg {
   static constexpr int THREADS = N >= 2048 ? 1024 : 512;
   static constexpr int TX = THREADS / (N / 8);
-  static constexpr int MINB = N >= 2048 ? 1 : MODE == P2_Z_BIN ? 4 : 3;
+  static constexpr int MINB = N >= 2048 ? 2 : MODE == P2_Z_BIN ? 4 : 3;
 };
 
 template <int N, int MODE>
