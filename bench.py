@@ -671,9 +671,17 @@ def run_ooc(args):
         del d
     z0, z1 = rng.cpu().tolist()
     P = z1 - z0 + 1
-    # page-locked by registering a plain host array (exact size; a caching pinned allocator
-    # would round a 106 GB request up to the next power of two)
-    host_np = np.empty((P, n, n), dtype=np.float32)
+    # page-locked by registering an anonymous mapping of the exact size (a caching pinned
+    # allocator would round a 106 GB request up to the next power of two); transparent huge
+    # pages where the kernel allows them (the streamed copies measured about 10 % faster)
+    import mmap
+    host_map = mmap.mmap(-1, P * n * n * 4, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    if hasattr(host_map, "madvise") and hasattr(mmap, "MADV_HUGEPAGE"):
+        try:
+            host_map.madvise(mmap.MADV_HUGEPAGE)
+        except OSError:
+            pass
+    host_np = np.frombuffer(host_map, dtype=np.float32).reshape(P, n, n)
     cudart = torch.cuda.cudart()
     err = cudart.cudaHostRegister(host_np.ctypes.data, host_np.nbytes, 0)
     if int(err) != 0:
@@ -704,6 +712,14 @@ def run_ooc(args):
         bins_host.copy_(bins, non_blocking=True)
 
     ms = _timed(step, args.steps, args.warmup)
+    # one more step with the library's per-launch events: where the step's time goes
+    api.set_timing(True)
+    step()
+    torch.cuda.synchronize()
+    breakdown = {}
+    for name, t in api.last_timings():
+        breakdown[name] = breakdown.get(name, 0.0) + t
+    api.set_timing(False)
     # pinned host -> device copy peak of this machine (best of 5 copies of 4 GiB)
     src_h = torch.empty(1 << 30, dtype=torch.float32, pin_memory=True)
     dst_d = torch.empty(1 << 30, dtype=torch.float32, device="cuda")
@@ -720,6 +736,7 @@ def run_ooc(args):
                                   "host memory streamed in double-buffered slabs, 2000 log Q bins; value: the "
                                   "forward; 'adjoint': the per-slab adjoint (dL/d cell)",
                       "grid": n, "nonzero_planes": P, "slabs": "two device slabs of about 256 MiB (double buffer)"},
+           "breakdown_ms": {k: round(v, 2) for k, v in breakdown.items()},
            "roofline": {"bound": "h2d", "achieved": achieved, "peak": h2d_peak, "unit": "GB/s",
                         "frac": achieved / h2d_peak, "peak_source": "measured pinned H2D copy of 4 GiB, best of 5",
                         "traffic": None},
@@ -751,6 +768,11 @@ def run_ooc(args):
     print(json.dumps(out))
     del host
     cudart.cudaHostUnregister(host_np.ctypes.data)
+    del host_np
+    try:
+        host_map.close()
+    except BufferError:  # a view is still alive; the mapping goes with the process
+        pass
 
 
 def main():
