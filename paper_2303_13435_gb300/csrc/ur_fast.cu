@@ -338,7 +338,6 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   // read here from the full k^2 -> bin table and used after the column loads.
   int lo_bin = 0, hi_bin = 0;
   if (MODE == P2_Z_BIN && binning) {
-    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
     if (threadIdx.x == 0) {
       s_blo = 0x7fffffff;
       s_bhi = -1;
@@ -357,7 +356,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
   const bool skip_mode = (MODE == P2_Z_BIN && binning && !a.fout) || (MODE == P2_Z_ADJ && binning);
   if (skip_mode) {
     // every thread votes for its own column (columns past the end count as beyond); in the
-    // forward the vote's barrier also makes the thresholds staged above visible
+    // forward the vote's barrier also publishes the range reset above
     const bool beyond = __syncthreads_and(!valid || c2 >= __ldg(a.thr + a.nbins));
     if (beyond) {  // uniform over the block
       // adjoint: the output columns are zero; unless the caller reads them as zeros
@@ -411,6 +410,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       const int li = j + q * T - a.zoff;
       v[q] = (valid && li >= 0 && li < a.nload) ? __ldg(a.src + sbase + (long long)li * a.S) : make_float2(0.f, 0.f);
     }
+  }
+  // forward z pass: the thresholds go to shared memory after the column loads are issued, so
+  // that the two latencies overlap (the adjoint stages its tables before its loads: staged
+  // after them, the loaded values stay live across the staging and spill at 40 registers)
+  if (MODE == P2_Z_BIN && binning) {
+    for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) thr[i] = __ldg(a.thr + i);
   }
   float2* line = buf + c * PITCH;
   if (binning && (MODE == P2_Z_ADJ || !skip_mode)) __syncthreads();  // tables (and the range reset) visible
