@@ -550,6 +550,15 @@ def run_batch(args):
     with torch.cuda.graph(graph, stream=s):
         batch_step()
     ms_graph = timed(graph.replay, args.steps)
+    # the looped path captured in one graph too: what is left of the batched form's advantage
+    # once both paths are free of launch overhead
+    with torch.cuda.stream(s):
+        loop_step()
+    torch.cuda.synchronize()
+    graph_loop = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_loop, stream=s):
+        loop_step()
+    ms_loop_graph = timed(graph_loop.replay, args.steps)
     # agreement of the two paths (same accuracy bar as the tests)
     loop_step()
     batch_step()
@@ -567,6 +576,7 @@ def run_batch(args):
                       "sizes": sorted({p.n for p in parts})},
            "batch": {"ms_looped_single_instance": ms_loop, "ms_batched_eager": ms_batch_eager,
                      "ms_batched_graph": ms_graph, "speedup_graph_vs_looped": ms_loop / ms_graph,
+                     "ms_looped_in_one_graph": ms_loop_graph,
                      "max_rel_diff_mean_I": worst, "autotune_seconds": tune_s,
                      "tiles": {str(k): list(v[:2]) for k, v in chosen.items()}}}
     print(json.dumps(out))
