@@ -23,33 +23,40 @@
 #include "ur_density.cuh"
 #include "ur_fast.cuh"
 
-template <int L>
+// E = values per thread: 8 (radix-8 stages) or 16 (radix-16 stages, used by the
+// column passes of the longest lines, where fewer exchanges per transform and
+// more values per barrier pay for the registers).
+template <int L, int E = 8>
 struct P2 {
   static constexpr int LOG = L == 8 ? 3 : L == 16 ? 4 : L == 32 ? 5 : L == 64 ? 6 : L == 128 ? 7 : L == 256 ? 8
                                                                                            : L == 512 ? 9 : L == 1024 ? 10
                                                                                            : L == 2048 ? 11 : 12;
-  static constexpr int T = L / 8;
-  static constexpr int NFULL = LOG / 3;
-  static constexpr int REM = LOG % 3;
+  static constexpr int LE = E == 16 ? 4 : 3;  // log2 E
+  static constexpr int T = L / E;
+  static constexpr int NFULL = LOG / LE;
+  static constexpr int REM = LOG % LE;
   static constexpr int NST = NFULL + (REM ? 1 : 0);
   static constexpr int PITCH = L + L / 16;
+  static_assert(E == 8 || E == 16, "8 or 16 values per thread");
 };
 
 __device__ __forceinline__ int p2pad(int i) { return i + (i >> 4); }
 
-constexpr int ipow8(int s) { return s == 0 ? 1 : 8 * ipow8(s - 1); }
+constexpr int ipowe(int e, int s) { return s == 0 ? 1 : e * ipowe(e, s - 1); }
 
 // Offset (float2) of stage S >= 1 in the stage twiddle table of an L-point transform:
-// the stages before S are radix 8, with 8^s rows of 8 slots each.
-constexpr int p2_stage_off(int S) { return S <= 1 ? 0 : p2_stage_off(S - 1) + 8 * ipow8(S - 1); }
+// the stages before S are radix E, with E^s rows of E slots each.
+template <int E>
+constexpr int p2_stage_off(int S) { return S <= 1 ? 0 : p2_stage_off<E>(S - 1) + E * ipowe(E, S - 1); }
 
-// Butterflies of stage S.  Thread j runs 8/R butterflies b = j + i L/8; the
-// inputs of butterfly i are v[i + (8/R) r], r < R; k = b mod NS; the twiddles
+// Butterflies of stage S.  Thread j runs E/R butterflies b = j + i L/E; the
+// inputs of butterfly i are v[i + (E/R) r], r < R; k = b mod NS; the twiddles
 // exp(-+2 pi i r k/(NS R)), r = 1 .. R-1, are row k of the stage's block of the
-// stage table (plan-built in float64, stored float32), read as 16-byte pairs.
-template <int L, int R, int NS, int S, bool INV>
-__device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const float2* __restrict__ stw) {
-  constexpr int T = L / 8, NB = 8 / R;
+// stage table (plan-built in float64, stored float32; E slots per row), read as
+// 16-byte pairs.
+template <int L, int E, int R, int NS, int S, bool INV>
+__device__ __forceinline__ void p2_butterflies(float2 (&v)[E], int j, const float2* __restrict__ stw) {
+  constexpr int T = L / E, NB = E / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = j + i * T;
@@ -58,7 +65,7 @@ __device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const floa
 #pragma unroll
     for (int r = 0; r < R; ++r) a[r] = v[i + NB * r];
     if constexpr (NS > 1) {
-      const float4* row = reinterpret_cast<const float4*>(stw + p2_stage_off(S) + k * 8);
+      const float4* row = reinterpret_cast<const float4*>(stw + p2_stage_off<E>(S) + k * E);
       float2 w[R];
 #pragma unroll
       for (int h = 0; h < R / 2; ++h) {
@@ -76,24 +83,24 @@ __device__ __forceinline__ void p2_butterflies(float2 (&v)[8], int j, const floa
 }
 
 // Barrier between the writers and readers of a line: the whole block, or only
-// the warp when every thread of the line sits in one warp (L/8 <= 32).
+// the warp when every thread of the line sits in one warp (L/E <= 32).
 template <bool WS>
 __device__ __forceinline__ void p2_sync(unsigned wmask) {
   if constexpr (WS) __syncwarp(wmask);
   else __syncthreads();
 }
 
-// lanes of the warp that hold the line of this thread (L/8 <= 32 threads per line)
+// lanes of the warp that hold the line of this thread (T <= 32 threads per line)
 template <int T>
 __device__ __forceinline__ unsigned p2_line_lanes() {
   if constexpr (T >= 32) return 0xffffffffu;
   else return ((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1));
 }
 
-// Stage outputs to shared memory at (b - k) R + k + r NS, then reload as j + q L/8.
-template <int L, int R, int NS, bool WS>
-__device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line, unsigned wmask) {
-  constexpr int T = L / 8, NB = 8 / R;
+// Stage outputs to shared memory at (b - k) R + k + r NS, then reload as j + q L/E.
+template <int L, int E, int R, int NS, bool WS>
+__device__ __forceinline__ void p2_exchange(float2 (&v)[E], int j, float2* line, unsigned wmask) {
+  constexpr int T = L / E, NB = E / R;
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = j + i * T;
@@ -103,33 +110,33 @@ __device__ __forceinline__ void p2_exchange(float2 (&v)[8], int j, float2* line,
   }
   p2_sync<WS>(wmask);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = line[p2pad(j + q * T)];
+  for (int q = 0; q < E; ++q) v[q] = line[p2pad(j + q * T)];
   p2_sync<WS>(wmask);
 }
 
-template <int L, bool INV, bool WS, int S>
+template <int L, int E, bool INV, bool WS, int S>
 struct P2Run {
-  __device__ static __forceinline__ void run(float2 (&v)[8], int j, float2* line, const float2* __restrict__ stw,
+  __device__ static __forceinline__ void run(float2 (&v)[E], int j, float2* line, const float2* __restrict__ stw,
                                              unsigned wmask) {
-    constexpr int NST = P2<L>::NST, NFULL = P2<L>::NFULL, REM = P2<L>::REM;
+    constexpr int NST = P2<L, E>::NST, NFULL = P2<L, E>::NFULL, REM = P2<L, E>::REM;
     if constexpr (S < NST) {
-      constexpr int R = (S < NFULL) ? 8 : (1 << REM);
-      constexpr int NS = ipow8(S);
-      p2_butterflies<L, R, NS, S, INV>(v, j, stw);
-      if constexpr (S + 1 < NST) p2_exchange<L, R, NS, WS>(v, j, line, wmask);
-      P2Run<L, INV, WS, S + 1>::run(v, j, line, stw, wmask);
+      constexpr int R = (S < NFULL) ? E : (1 << REM);
+      constexpr int NS = ipowe(E, S);
+      p2_butterflies<L, E, R, NS, S, INV>(v, j, stw);
+      if constexpr (S + 1 < NST) p2_exchange<L, E, R, NS, WS>(v, j, line, wmask);
+      P2Run<L, E, INV, WS, S + 1>::run(v, j, line, stw, wmask);
     }
   }
 };
 
 // Whole line transform.  WS = false: every thread of the block must call it
-// (block barriers); WS = true: the L/8 threads of a line share a warp and all
+// (block barriers); WS = true: the L/E threads of a line share a warp and all
 // of them (the lanes in wmask) must call it.  stw: the stage twiddle table of
-// the L-point transform.
-template <int L, bool INV, bool WS = false>
-__device__ __forceinline__ void p2_fft(float2 (&v)[8], int j, float2* line, const float2* __restrict__ stw,
+// the L-point transform for E values per thread.
+template <int L, bool INV, bool WS = false, int E = 8>
+__device__ __forceinline__ void p2_fft(float2 (&v)[E], int j, float2* line, const float2* __restrict__ stw,
                                        unsigned wmask = 0xffffffffu) {
-  P2Run<L, INV, WS, 0>::run(v, j, line, stw, wmask);
+  P2Run<L, E, INV, WS, 0>::run(v, j, line, stw, wmask);
 }
 
 // ---------------------------------------------------------------------------
@@ -288,26 +295,29 @@ __global__ void __launch_bounds__(512, 3) k_p2_rows(RowArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Columns.  Block = TX columns x L/8 threads; thread (j, c), c fastest, so a
+// Columns.  Block = TX columns x L/E threads; thread (j, c), c fastest, so a
 // warp reads whole row segments of TX consecutive columns.
 // ---------------------------------------------------------------------------
 enum { P2_Y_FWD = 0, P2_Y_INV = 1, P2_Z_BIN = 2, P2_Z_ADJ = 3 };
 
-// threads per column block: 512, or 1024 for N >= 2048 so that a block still
-// spans at least two columns (16-byte row segments) of the half spectrum
-// MINB: resident blocks per SM the register budget is cut for (the z pass
-// with binning fits in 32 registers: four blocks of 512 threads)
+// E: values per thread (ur_fast_col_e); threads per column block: 512, or 1024
+// for N >= 2048 so that a block still spans at least two columns (16-byte row
+// segments) of the half spectrum.  MINB: resident blocks per SM the register
+// budget is cut for (the z pass with binning fits in 32 registers: four blocks
+// of 512 threads; 16 values per thread take 64)
 template <int N, int MODE = P2_Y_FWD>
 struct ColCfg {
+  static constexpr int E = UR_FAST_COL_E(N);
   static constexpr int THREADS = N >= 2048 ? 1024 : 512;
-  static constexpr int TX = THREADS / (N / 8);
-  static constexpr int MINB = N >= 2048 ? 2 : MODE == P2_Z_BIN ? 4 : 3;
+  static constexpr int TX = THREADS / (N / E);
+  static constexpr int MINB = E == 16 ? 65536 / (64 * THREADS) : N >= 2048 ? 2 : MODE == P2_Z_BIN ? 4 : 3;
 };
 
 template <int N, int MODE>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k_p2_cols(ColArgs a) {
   // column pitch = 2 (mod 16) float2: the TX columns a warp touches fall on different banks
-  constexpr int T = N / 8, TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
+  constexpr int E = ColCfg<N>::E;
+  constexpr int T = N / E, TX = ColCfg<N>::TX, PITCH = P2<N>::PITCH + 2, H = N / 2 + 1, M = N / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_blo, s_bhi;
   float2* buf = reinterpret_cast<float2*>(smraw);
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       if (MODE == P2_Z_ADJ && valid && a.k2_zero == 0x7fffffff) {
         const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = make_float2(0.f, 0.f);
+        for (int q = 0; q < E; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = make_float2(0.f, 0.f);
       }
       return;
     }
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) hs[i] = __ldg(a.sigma + i);
   }
   const long long sbase = (long long)(col / H) * a.A + (col - (col / H) * H);
-  float2 v[8];
+  float2 v[E];
   if (MODE == P2_Y_FWD && a.row_skip) {
     // forward y pass over a generated sphere: rows y outside the particle in plane z are
     // zero and were not written by the row pass
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     const long long step = (long long)T * a.S;
     const int z = a.gen_z0 + col / H;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < E; ++q) {
       const int y = j + q * T;
       v[q] = (valid && !sphere_row_empty(a.sh, y, z)) ? __ldg(src + q * step) : make_float2(0.f, 0.f);
     }
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     const long long step = (long long)T * a.S;
     const int kx2 = kx * kx;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < E; ++q) {
       const int li = j + q * T, kyy = li < M ? li : li - N;
       v[q] = (valid && kx2 + kyy * kyy < a.k2_zero) ? __ldg(src + q * step) : make_float2(0.f, 0.f);
     }
@@ -403,10 +413,10 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     const float2* src = a.src + (valid ? sbase + (long long)j * a.S : 0);
     const long long step = (long long)T * a.S;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __ldg(src + q * step);
+    for (int q = 0; q < E; ++q) v[q] = __ldg(src + q * step);
   } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < E; ++q) {
       const int li = j + q * T - a.zoff;
       v[q] = (valid && li >= 0 && li < a.nload) ? __ldg(a.src + sbase + (long long)li * a.S) : make_float2(0.f, 0.f);
     }
@@ -426,17 +436,17 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
     atomicMax(&s_bhi, hi_bin);
   }
   if (MODE == P2_Y_FWD || MODE == P2_Y_INV) {
-    p2_fft<N, MODE == P2_Y_INV>(v, j, line, a.stw);
+    p2_fft<N, MODE == P2_Y_INV, false, E>(v, j, line, a.stw);
     if (valid) {
       const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+      for (int q = 0; q < E; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
     }
   } else if (MODE == P2_Z_BIN) {
-    p2_fft<N, false>(v, j, line, a.stw);
+    p2_fft<N, false, false, E>(v, j, line, a.stw);
     if (a.fout && valid) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a.fout[(long long)(j + q * T) * N * H + col] = cscale(v[q], a.fscale);
+      for (int q = 0; q < E; ++q) a.fout[(long long)(j + q * T) * N * H + col] = cscale(v[q], a.fscale);
     }
     if (binning) {
       // task = (column, chunk of CH consecutive |kz| = m); at most one task per thread.
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       }
       // natural order in shared memory
 #pragma unroll
-      for (int q = 0; q < 8; ++q) line[p2pad(j + q * T)] = v[q];
+      for (int q = 0; q < E; ++q) line[p2pad(j + q * T)] = v[q];
       __syncthreads();
       if (has) {
         const float2* ln = buf + tc * PITCH;
@@ -532,28 +542,28 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, (ColCfg<N, MODE>::MINB)) k
       }
     }
   } else {  // P2_Z_ADJ
-    if (!a.skip_fwd) p2_fft<N, false>(v, j, line, a.stw);
+    if (!a.skip_fwd) p2_fft<N, false, false, E>(v, j, line, a.stw);
     // scale of element kz: sigma of the bin of k^2 = c2 + m^2, m = |signed kz|
     const int nb = a.nbins;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < E; ++q) {
       const int kz = j + q * T;
       const int m = kz <= M ? kz : N - kz;
       const int b = bin_rank(crs, a.crs_shift, thr, nb, c2 + m * m);
       v[q] = cscale(v[q], (b >= 0 && b < nb) ? hs[b] : 0.f);
     }
-    p2_fft<N, true>(v, j, line, a.stw);
+    p2_fft<N, true, false, E>(v, j, line, a.stw);
     if (valid) {
       const long long dbase = (long long)(col / H) * a.Ad + (col - (col / H) * H);
       if (a.out_cnt > 0) {  // a slab of output planes
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < E; ++q) {
           const int zo = j + q * T - a.out_lo;
           if (zo >= 0 && zo < a.out_cnt) a.dst[dbase + (long long)zo * a.Sd] = v[q];
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
+        for (int q = 0; q < E; ++q) a.dst[dbase + (long long)(j + q * T) * a.Sd] = v[q];
       }
     }
   }

@@ -202,30 +202,31 @@ extern "C" int64_t ur_selftest_fastdiv(void) {
   return bad;
 }
 
-// Stage twiddles of the compile-time power-of-two transforms of length L = 2^lg:
-// radix-8 Stockham stages (the last one radix 4 or 2 when lg is not a multiple of 3).
-// Stage S >= 1 has NS = 8^S butterfly classes k and radix R; its rows hold
-// exp(-2 pi i r k / (NS R)) for r < R at row k (8 slots, unused ones 0), so a
-// butterfly reads its R - 1 twiddles with at most four 16-byte loads.  Row blocks
-// follow each other by stage.  Returns the number of float2 written (out may be
-// NULL to count).
-static size_t stage_twiddles(int lg, float2* out) {
-  const int nfull = lg / 3, rem = lg % 3, nst = nfull + (rem ? 1 : 0);
+// Stage twiddles of the compile-time power-of-two transforms of length L = 2^lg
+// with E = 8 or 16 values per thread: radix-E Stockham stages (the last one of a
+// smaller radix when lg is not a multiple of log2 E).  Stage S >= 1 has NS = E^S
+// butterfly classes k and radix R; its rows hold exp(-2 pi i r k / (NS R)) for
+// r < R at row k (E slots, unused ones 0), so a butterfly reads its R - 1
+// twiddles with at most E/2 16-byte loads.  Row blocks follow each other by
+// stage.  Returns the number of float2 written (out may be NULL to count).
+static size_t stage_twiddles(int lg, int E, float2* out) {
+  const int le = E == 16 ? 4 : 3;
+  const int nfull = lg / le, rem = lg % le, nst = nfull + (rem ? 1 : 0);
   size_t off = 0;
   long long ns = 1;
   for (int st = 0; st < nst; ++st) {
-    const int R = st < nfull ? 8 : (1 << rem);
+    const int R = st < nfull ? E : (1 << rem);
     if (st >= 1) {
       for (long long k = 0; k < ns; ++k)
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < E; ++r) {
           float2 w = make_float2(0.f, 0.f);
           if (r < R) {
             const double a = 2.0 * M_PI * (double)(r * k) / (double)(ns * R);
             w = make_float2((float)cos(a), (float)(-sin(a)));
           }
-          if (out) out[off + (size_t)k * 8 + r] = w;
+          if (out) out[off + (size_t)k * E + r] = w;
         }
-      off += (size_t)ns * 8;
+      off += (size_t)ns * E;
     }
     ns *= R;
   }
@@ -416,10 +417,12 @@ extern "C" ur_status ur_plan_create(const ur_grid_desc* g, const double* edges, 
   if (ur_fast_supported(n)) {
     int lg = 0;
     while ((1 << lg) < n) ++lg;
-    const size_t cn = stage_twiddles(lg, nullptr), cm = stage_twiddles(lg - 1, nullptr);
+    // columns (N points) run UR_FAST_COL_E(n) values per thread, rows (N/2 points) 8
+    const int ecol = UR_FAST_COL_E(n);
+    const size_t cn = stage_twiddles(lg, ecol, nullptr), cm = stage_twiddles(lg - 1, 8, nullptr);
     float2* st_h = (float2*)malloc(sizeof(float2) * (cn + cm + 1));
-    stage_twiddles(lg, st_h);
-    stage_twiddles(lg - 1, st_h + cn);
+    stage_twiddles(lg, ecol, st_h);
+    stage_twiddles(lg - 1, 8, st_h + cn);
     p->stw_m_off = (int)cn;
     const cudaError_t ea = cudaMalloc(&p->stw, sizeof(float2) * (cn + cm + 1));
     const cudaError_t eb = ea == cudaSuccess ? cudaMemcpy(p->stw, st_h, sizeof(float2) * (cn + cm + 1),

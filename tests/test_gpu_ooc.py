@@ -114,7 +114,10 @@ def test_streamed_2048_cube_parseval_counts_and_device_path():
     dev = host.cuda()
     ref = api.fft_intensity(plan, dev).cpu().numpy()
     assert np.array_equal(bins[0], ref[0])
-    assert np.allclose(bins[1:4], ref[1:4], rtol=2e-5, atol=0)
+    # two runs of the same pass differ in the last bits (float32 block sums; each bin's shift is the
+    # first value a block publishes, so block order decides it): up to 2.4e-5 on sum I^2 measured
+    # between two device-resident runs; the gate is the I(Q) tolerance
+    assert np.allclose(bins[1:4], ref[1:4], rtol=1e-4, atol=0)
 
 
 def test_streamed_1024_sampled_k_against_direct_eq1():
