@@ -605,14 +605,17 @@ def test_large_grid_adjoint_directional_derivative(n, keep_f):
         b = api.fft_intensity_tiled(plan, cc, shape, weights=wts, ws=ws)
         return float((c * torch.nan_to_num(b[4].double(), nan=0.0)).sum().item())
 
-    d = (torch.randn(cell.shape, generator=g) * 0.01 * float(cell.abs().mean())).cuda()
+    # L is quadratic in the cell and in the weights, so the central difference has no truncation
+    # error and the step can be large: a 10 % step keeps the forwards' run-to-run rounding (about
+    # 3e-6 of each bin mean) far below the difference itself
+    d = (torch.randn(cell.shape, generator=g) * 0.1 * float(cell.abs().mean())).cuda()
     fd = (loss(cell + d, weights) - loss(cell - d, weights)) / 2.0
     an = float((dcell.double() * d.double()).sum().item())
     print(n, "dL/du", fd, an)
     assert math.isclose(fd, an, rel_tol=2e-3), (fd, an)
     if weights is not None:
         e = torch.zeros_like(weights)
-        e[z0:z0 + nz] = (torch.randn((nz, n, n), generator=g) * 0.01).cuda()
+        e[z0:z0 + nz] = (torch.randn((nz, n, n), generator=g) * 0.1).cuda()
         fdm = (loss(cell, weights + e) - loss(cell, weights - e)) / 2.0
         anm = float((dmask.double() * e.double()).sum().item())
         print(n, "dL/dm", fdm, anm)
