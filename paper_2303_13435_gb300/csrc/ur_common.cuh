@@ -409,7 +409,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ buf, int pitch, i
 template <int R, bool INV, int EMAX>
 __device__ __forceinline__ int fft_stages_of(float2* buf, int pitch, int lines, const StageInfo* st, int nst,
                                              const float2* __restrict__ tw, int i) {
-  while (i < nst) {
+  while (i < nst) {  // nst: one past the last stage to run
     const StageInfo si = st[i];  // shared memory (fft_lines): a broadcast read per stage
     if (si.R != R) break;
     fft_stage<R, INV, EMAX>(buf, pitch, lines, si, tw);
@@ -443,6 +443,143 @@ __device__ __forceinline__ void fft_lines(float2* buf, int pitch, int lines, con
   i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
   i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, s_st, nst, tw, i);
+}
+
+// First stage (Ns = 1, no twiddles) with inputs from `ld(line, i)` instead of shared
+// memory, and last stage (k = j, outputs at j + r Ns) handing its outputs to
+// `st(line, i, v)`.  Their butterflies are mapped line-fastest (w = j lines + line), so
+// consecutive threads take the same position of consecutive lines: a tile of columns is
+// read and written in row segments.
+template <int R, bool INV, int EMAX, bool LF, class Ld>
+__device__ __forceinline__ void fft_first_stage(float2* __restrict__ buf, int pitch, int lines, const FastDiv& dl,
+                                                const StageInfo& si, Ld ld) {
+  constexpr int BMAX = (EMAX + R - 1) / R;
+  const int nb = si.nb;
+  const int total = lines * nb;
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    const int w = threadIdx.x + b * blockDim.x;
+    if (w < total) {
+      int j, line;
+      if constexpr (LF) {
+        j = (int)dl.div((uint32_t)w);
+        line = w - j * lines;
+      } else {
+        line = (int)si.div_nb.div((uint32_t)w);
+        j = w - line * nb;
+      }
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = ld(line, j + r * nb);
+      dft<R, INV>(v);
+      float2* dst = buf + line * pitch + j * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r] = v[r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int R, bool INV, int EMAX, bool LF, class St>
+__device__ __forceinline__ void fft_last_stage(const float2* __restrict__ buf, int pitch, int lines,
+                                               const FastDiv& dl, const StageInfo& si,
+                                               const float2* __restrict__ tw, St st) {
+  constexpr int BMAX = (EMAX + R - 1) / R;
+  const int nb = si.nb;
+  const int total = lines * nb;
+#pragma unroll
+  for (int b = 0; b < BMAX; ++b) {
+    const int w = threadIdx.x + b * blockDim.x;
+    if (w < total) {
+      int j, line;
+      if constexpr (LF) {
+        j = (int)dl.div((uint32_t)w);
+        line = w - j * lines;
+      } else {
+        line = (int)si.div_nb.div((uint32_t)w);
+        j = w - line * nb;
+      }
+      const float2* src = buf + line * pitch + j;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src[r * nb];
+      if (j > 0) {  // last stage: Ns = nb, so k = j
+        const int step = j * si.tstep;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = twmul<INV>(v[r], ld_twiddle(tw + r * step));
+      }
+      dft<R, INV>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(line, j + r * nb, v[r]);
+    }
+  }
+}
+
+template <bool INV, int EMAX, bool LF, class Ld>
+__device__ __forceinline__ void fft_first_any(float2* buf, int pitch, int lines, const FastDiv& dl,
+                                              const StageInfo& si, Ld ld) {
+  switch (si.R) {
+    case 8: fft_first_stage<8, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 4: fft_first_stage<4, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 2: fft_first_stage<2, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 6: fft_first_stage<6, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 10: fft_first_stage<10, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 9: fft_first_stage<9, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 3: fft_first_stage<3, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    case 5: fft_first_stage<5, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+    default: fft_first_stage<7, INV, EMAX, LF>(buf, pitch, lines, dl, si, ld); break;
+  }
+}
+
+template <bool INV, int EMAX, bool LF, class St>
+__device__ __forceinline__ void fft_last_any(const float2* buf, int pitch, int lines, const FastDiv& dl,
+                                             const StageInfo& si, const float2* tw, St st) {
+  switch (si.R) {
+    case 8: fft_last_stage<8, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 4: fft_last_stage<4, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 2: fft_last_stage<2, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 6: fft_last_stage<6, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 10: fft_last_stage<10, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 9: fft_last_stage<9, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 3: fft_last_stage<3, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    case 5: fft_last_stage<5, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+    default: fft_last_stage<7, INV, EMAX, LF>(buf, pitch, lines, dl, si, tw, st); break;
+  }
+}
+
+// FFT of `lines` lines.  With LOAD the first stage reads global memory through `ld`
+// (otherwise the lines are in shared memory already); with STORE the last stage writes
+// global memory through `st` (otherwise the result stays in shared memory, as with
+// fft_lines).  LF: the two stages map butterflies line-fastest (tiles of columns, read
+// in row segments) or position-fastest (rows, read along the row).  Needs nst >= 2.
+// Every thread of the block must call it; with STORE the caller synchronises before it
+// reuses buf.
+template <bool INV, int EMAX, bool LOAD, bool STORE, bool LF, class Ld, class St>
+__device__ __forceinline__ void fft_lines_io(float2* buf, int pitch, int lines, const StageInfo* __restrict__ st,
+                                             int nst, const float2* __restrict__ tw, Ld ld, St stf) {
+  constexpr int W = (int)(sizeof(StageInfo) / 4);
+  __shared__ __align__(16) uint32_t s_raw[UR_MAX_STAGES * W];
+  const StageInfo* s_st = reinterpret_cast<const StageInfo*>(s_raw);
+  __syncthreads();  // an earlier call of this kernel may still read s_raw or buf
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(st);
+    for (int w = threadIdx.x; w < nst * W; w += blockDim.x) s_raw[w] = __ldg(src + w);
+  }
+  __syncthreads();
+  const FastDiv dl((uint32_t)lines);
+  if constexpr (LOAD) fft_first_any<INV, EMAX, LF>(buf, pitch, lines, dl, s_st[0], ld);
+  const int iend = STORE ? nst - 1 : nst;
+  int i = LOAD ? 1 : 0;
+  i = fft_stages_of<8, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<4, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<2, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<6, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<10, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<9, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<3, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<5, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  i = fft_stages_of<7, INV, EMAX>(buf, pitch, lines, s_st, iend, tw, i);
+  if constexpr (STORE) fft_last_any<INV, EMAX, LF>(buf, pitch, lines, dl, s_st[nst - 1], tw, stf);
 }
 
 // ---------------------------------------------------------------------------

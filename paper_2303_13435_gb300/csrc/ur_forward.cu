@@ -42,6 +42,13 @@ __device__ __forceinline__ float2 load_pair<__half>(const __half* p) {
   return __half22float2(h);
 }
 
+struct NoLd {
+  __device__ __forceinline__ float2 operator()(int, int) const { return make_float2(0.f, 0.f); }
+};
+struct NoSt {
+  __device__ __forceinline__ void operator()(int, int, float2) const {}
+};
+
 // GEN = 1: the row's density is generated here (Sec. 2.3 tile + mask) instead of read.
 // Body of one block (block index blk); shared by the single-plan and batched launches.
 template <int GEN, typename T>
@@ -155,6 +162,34 @@ __device__ __forceinline__ void store_columns(const ColArgs& a, const ColDivs& d
     if (c < a.ncols) a.dst[col_offset((uint32_t)c, dv.h, a.Ad) + (long long)i * a.Sd] = buf[t * a.pitch + i];
   }
 }
+
+// Element access of the first and last transform stages (fft_lines_io): element i of
+// tile line `line` (column c0 + line) in the source or destination layout.
+struct ColLd {
+  const float2* src;
+  long long A, S, ncols, c0;
+  int zoff, nload;
+  FastDiv h;
+  __device__ ColLd(const ColArgs& a, const ColDivs& dv, long long c)
+      : src(a.src), A(a.A), S(a.S), ncols(a.ncols), c0(c), zoff(a.zoff), nload(a.nload), h(dv.h) {}
+  __device__ __forceinline__ float2 operator()(int line, int i) const {
+    const long long c = c0 + line;
+    const int li = i - zoff;
+    if (c < ncols && li >= 0 && li < nload) return __ldg(src + col_offset((uint32_t)c, h, A) + (long long)li * S);
+    return make_float2(0.f, 0.f);
+  }
+};
+struct ColSt {
+  float2* dst;
+  long long Ad, Sd, ncols, c0;
+  FastDiv h;
+  __device__ ColSt(const ColArgs& a, const ColDivs& dv, long long c)
+      : dst(a.dst), Ad(a.Ad), Sd(a.Sd), ncols(a.ncols), c0(c), h(dv.h) {}
+  __device__ __forceinline__ void operator()(int line, int i, float2 v) const {
+    const long long c = c0 + line;
+    if (c < ncols) dst[col_offset((uint32_t)c, h, Ad) + (long long)i * Sd] = v;
+  }
+};
 
 // Walk the (column, |kz|) pairs of the block's spectrum columns in chunks of
 // BIN_CHUNK consecutive |kz| = m.  k^2 = kx^2 + ky^2 + m^2 grows with m, so the
@@ -295,12 +330,25 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
     }
   }
   {
-    load_columns(a, dv, buf, c0, N);
+    // with two or more stages the first stage reads the columns from global memory and, where
+    // the result goes back to global memory, the last stage writes it (no staging round trips)
+    const bool io = a.nst >= 2;
     if (MODE == COL_Y) {
-      fft_lines<INV, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
-      store_columns(a, dv, buf, c0, N);
+      if (io) {
+        fft_lines_io<INV, UR_EMAX, true, true, true>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw, ColLd(a, dv, c0),
+                                               ColSt(a, dv, c0));
+      } else {
+        load_columns(a, dv, buf, c0, N);
+        fft_lines<INV, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+        store_columns(a, dv, buf, c0, N);
+      }
     } else if (MODE == COL_ZBIN) {
-      fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      if (io) {
+        fft_lines_io<false, UR_EMAX, true, false, true>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw, ColLd(a, dv, c0), NoSt());
+      } else {
+        load_columns(a, dv, buf, c0, N);
+        fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      }
       if (a.fout) {
         for (int f = threadIdx.x; f < a.TX * N; f += blockDim.x) {
           const int i = (int)dv.tx.div((uint32_t)f);
@@ -314,12 +362,21 @@ __device__ __forceinline__ void cols_body(const ColArgs& a, long long blk) {
         walk_bins(a, dv, thr, c0, acc);
       }
     } else {  // COL_ZADJ: F along z (recomputed or given), times sigma(bin), inverse along z
-      if (!a.skip_fwd) fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      if (io && !a.skip_fwd) {
+        fft_lines_io<false, UR_EMAX, true, false, true>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw, ColLd(a, dv, c0), NoSt());
+      } else {
+        load_columns(a, dv, buf, c0, N);
+        if (!a.skip_fwd) fft_lines<false, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+      }
       SigmaScale sc{buf, a.pitch, a.M, N, a.nbins, a.sigma};
       walk_bins(a, dv, thr, c0, sc);
       __syncthreads();
-      fft_lines<true, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
-      store_columns(a, dv, buf, c0, N);
+      if (io) {
+        fft_lines_io<true, UR_EMAX, false, true, true>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw, NoLd(), ColSt(a, dv, c0));
+      } else {
+        fft_lines<true, UR_EMAX>(buf, a.pitch, a.TX, a.sched, a.nst, a.tw);
+        store_columns(a, dv, buf, c0, N);
+      }
     }
   }
   if (MODE == COL_ZBIN && a.nbins > 0) {
