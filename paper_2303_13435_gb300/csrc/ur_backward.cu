@@ -36,6 +36,10 @@ __global__ void k_sigma(const double* __restrict__ g, const double* __restrict__
 // Each row: Y[z][y][0..M] (Hermitian half along x) -> Z[k] = E[k] + i O[k],
 //   E[k] = X[k] + conj X[M-k],  O[k] = (X[k] - conj X[M-k]) conj(W_N^k),
 // then z = IFFT_{M}(Z) gives (g(2m), g(2m+1)) = (Re z[m], Im z[m]).
+struct NoStore {
+  __device__ __forceinline__ void operator()(int, int, float2) const {}
+};
+
 __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int by) {
   const float2* __restrict__ Y = g.Y;
   const int N = g.N, RB = g.RB, nst = g.nst, U = g.U, ox = g.ox, oy = g.oy, oz = g.oz;
@@ -64,46 +68,65 @@ __device__ __forceinline__ void rows_grad_body(const GenGradArgs& g, int bx, int
   __syncthreads();
   {
     const int nb = min(RB, nrows - r0);
-    // load rows
-    for (int f = threadIdx.x; f < RB * H; f += blockDim.x) {
-      const int t = (int)dH.div((uint32_t)f);
-      const int k = f - t * H;
-      float2 v = make_float2(0.f, 0.f);
-      if (t < nb) {
+    if (nst >= 2) {
+      // the first stage packs its inputs straight from the Hermitian half rows (no staging
+      // round trip): Z[i] = (X[i] + conj X[M-i]) + i (X[i] - conj X[M-i]) conj(W_N^i), X[M] for i = 0
+      auto packed = [&](int t, int i) -> float2 {
+        if (t >= nb) return make_float2(0.f, 0.f);
         const int q = r0 + t;
         const int a = (int)dNy.div((uint32_t)q);
         const int b = q - a * nyr;
         const long long z = zf + (long long)U * a, y = yf + (long long)U * b;
-        v = __ldg(Y + (z * N + y) * H + k);
+        const float2* row = Y + (z * N + y) * H;
+        const float2 xa = __ldg(row + i), xb = __ldg(row + (M - i));
+        const float2 w = __ldg(tw + i);
+        const float2 e = cadd(xa, cconj(xb));
+        const float2 d = csub(xa, cconj(xb));
+        const float2 o = make_float2(d.x * w.x + d.y * w.y, d.y * w.x - d.x * w.y);  // * conj(W^i)
+        return make_float2(e.x - o.y, e.y + o.x);
+      };
+      fft_lines_io<true, UR_EMAX, true, false, false>(buf, H, RB, sched, nst, tw, packed, NoStore());
+    } else {
+      for (int f = threadIdx.x; f < RB * H; f += blockDim.x) {
+        const int t = (int)dH.div((uint32_t)f);
+        const int k = f - t * H;
+        float2 v = make_float2(0.f, 0.f);
+        if (t < nb) {
+          const int q = r0 + t;
+          const int a = (int)dNy.div((uint32_t)q);
+          const int b = q - a * nyr;
+          const long long z = zf + (long long)U * a, y = yf + (long long)U * b;
+          v = __ldg(Y + (z * N + y) * H + k);
+        }
+        buf[f] = v;
       }
-      buf[f] = v;
-    }
-    __syncthreads();
-    // Hermitian half -> packed complex sequence, in place by (k, M-k) pairs
-    const int half = M / 2 + 1;
-    const FastDiv dhalf((uint32_t)half);
-    for (int f = threadIdx.x; f < RB * half; f += blockDim.x) {
-      const int t = (int)dhalf.div((uint32_t)f);
-      const int k = f - t * half;
-      float2* X = buf + t * H;
-      const float2 xa = X[k], xb = X[M - k];
-      const float2 wa = __ldg(tw + k);
-      // Z[k]
-      const float2 ea = cadd(xa, cconj(xb));
-      const float2 da = csub(xa, cconj(xb));
-      const float2 oa = make_float2(da.x * wa.x + da.y * wa.y, da.y * wa.x - da.x * wa.y);  // * conj(W^k)
-      const float2 za = make_float2(ea.x - oa.y, ea.y + oa.x);
-      if (k != 0 && 2 * k != M) {
-        const float2 wb = __ldg(tw + (M - k));
-        const float2 eb = cadd(xb, cconj(xa));
-        const float2 db = csub(xb, cconj(xa));
-        const float2 ob = make_float2(db.x * wb.x + db.y * wb.y, db.y * wb.x - db.x * wb.y);
-        X[M - k] = make_float2(eb.x - ob.y, eb.y + ob.x);
+      __syncthreads();
+      // Hermitian half -> packed complex sequence, in place by (k, M-k) pairs
+      const int half = M / 2 + 1;
+      const FastDiv dhalf((uint32_t)half);
+      for (int f = threadIdx.x; f < RB * half; f += blockDim.x) {
+        const int t = (int)dhalf.div((uint32_t)f);
+        const int k = f - t * half;
+        float2* X = buf + t * H;
+        const float2 xa = X[k], xb = X[M - k];
+        const float2 wa = __ldg(tw + k);
+        // Z[k]
+        const float2 ea = cadd(xa, cconj(xb));
+        const float2 da = csub(xa, cconj(xb));
+        const float2 oa = make_float2(da.x * wa.x + da.y * wa.y, da.y * wa.x - da.x * wa.y);  // * conj(W^k)
+        const float2 za = make_float2(ea.x - oa.y, ea.y + oa.x);
+        if (k != 0 && 2 * k != M) {
+          const float2 wb = __ldg(tw + (M - k));
+          const float2 eb = cadd(xb, cconj(xa));
+          const float2 db = csub(xb, cconj(xa));
+          const float2 ob = make_float2(db.x * wb.x + db.y * wb.y, db.y * wb.x - db.x * wb.y);
+          X[M - k] = make_float2(eb.x - ob.y, eb.y + ob.x);
+        }
+        X[k] = za;
       }
-      X[k] = za;
+      __syncthreads();
+      fft_lines<true, UR_EMAX>(buf, H, RB, sched, nst, tw);
     }
-    __syncthreads();
-    fft_lines<true, UR_EMAX>(buf, H, RB, sched, nst, tw);
     // epilogue
     for (int f = threadIdx.x; f < RB * M; f += blockDim.x) {
       const int t = (int)dM.div((uint32_t)f);
