@@ -91,3 +91,23 @@ def normwise(a, b) -> float:
 def oracle_grads(rho64, cell, mask, dx, edges, g, count, origin=(0, 0, 0)):
     grho = adjoint.grad_rho(rho64, dx, edges, g, count=count)
     return adjoint.grad_cell_and_mask(grho, cell, mask, origin)
+
+
+def oracle_parity_counts(n, dx, edges):
+    """Per bin of the oracle's binning: voxels of the grid with kx even, and all voxels.  The
+    number of k with kx^2 + ky^2 + kz^2 = s is the convolution of the three axes' histograms of
+    k^2 (integer counts, convolved exactly by FFT in float64 and rounded); each s then takes the
+    oracle's bin of q(s)."""
+    k = scatter.signed_freq(n)
+    smax = 3 * (n // 2) ** 2
+    h_all = np.bincount(k * k, minlength=smax + 1).astype(np.float64)
+    h_even = np.bincount((k * k)[k % 2 == 0], minlength=smax + 1).astype(np.float64)
+    m = 1 << int(np.ceil(np.log2(3 * (smax + 1))))
+    fa = np.fft.rfft(h_all, m)
+    h3_even = np.rint(np.fft.irfft(np.fft.rfft(h_even, m) * fa * fa, m)[:smax + 1]).astype(np.int64)
+    h3_all = np.rint(np.fft.irfft(fa * fa * fa, m)[:smax + 1]).astype(np.int64)
+    j = scatter.bin_of_q(scatter.q_of_k2(np.arange(smax + 1), n, dx), edges)
+    nb = len(edges) - 1
+    ok = j >= 0
+    return (np.bincount(j[ok], weights=h3_even[ok], minlength=nb).astype(np.int64),
+            np.bincount(j[ok], weights=h3_all[ok], minlength=nb).astype(np.int64))

@@ -12,7 +12,8 @@ import torch
 from oracle import adjoint, density, merge as omerge, scatter
 from paper_2303_13435_gb300 import api, build, inputs
 
-from _cases import (GRAD_RTOL, compare_bins, normwise, oracle_density, oracle_forward, oracle_grads)
+from _cases import (GRAD_RTOL, compare_bins, normwise, oracle_density, oracle_forward, oracle_grads,
+                    oracle_parity_counts)
 
 pytestmark = pytest.mark.gpu
 
@@ -355,26 +356,6 @@ def test_single_voxel_bins_every_voxel_exactly(n, nbins, tma):
         assert np.array_equal(np.rint(voxels).astype(np.int64), want)
 
 
-def _oracle_parity_counts(n, dx, edges):
-    """Per bin of the oracle's binning: voxels of the grid with kx even, and all voxels.  The
-    number of k with kx^2 + ky^2 + kz^2 = s is the convolution of the three axes' histograms of
-    k^2 (integer counts, convolved exactly by FFT in float64 and rounded); each s then takes the
-    oracle's bin of q(s)."""
-    k = scatter.signed_freq(n)
-    smax = 3 * (n // 2) ** 2
-    h_all = np.bincount(k * k, minlength=smax + 1).astype(np.float64)
-    h_even = np.bincount((k * k)[k % 2 == 0], minlength=smax + 1).astype(np.float64)
-    m = 1 << int(np.ceil(np.log2(3 * (smax + 1))))
-    fa = np.fft.rfft(h_all, m)
-    h3_even = np.rint(np.fft.irfft(np.fft.rfft(h_even, m) * fa * fa, m)[:smax + 1]).astype(np.int64)
-    h3_all = np.rint(np.fft.irfft(fa * fa * fa, m)[:smax + 1]).astype(np.int64)
-    j = scatter.bin_of_q(scatter.q_of_k2(np.arange(smax + 1), n, dx), edges)
-    nb = len(edges) - 1
-    ok = j >= 0
-    return (np.bincount(j[ok], weights=h3_even[ok], minlength=nb).astype(np.int64),
-            np.bincount(j[ok], weights=h3_all[ok], minlength=nb).astype(np.int64))
-
-
 @pytest.mark.parametrize("n,nbins,tma", [(512, 512, False), (512, 512, True), (256, 200, False), (256, 200, True),
                                          (2048, 1000, False), (4096, 2000, False), (126, 96, False)])
 def test_two_voxel_bins_count_every_voxel(n, nbins, tma):
@@ -395,7 +376,7 @@ def test_two_voxel_bins_count_every_voxel(n, nbins, tma):
         plan.set_tma_zpass(True)
         assert plan.tma_zpass()
     gb = api.fft_intensity(plan, ed).cpu().numpy()
-    even, total = _oracle_parity_counts(n, dx, edges)
+    even, total = oracle_parity_counts(n, dx, edges)
     assert np.array_equal(gb[0].astype(np.int64), total)
     per_voxel = float(np.float32(1.0 / n ** 3)) * n ** 3
     got = gb[1] * float(n) ** 6 / per_voxel

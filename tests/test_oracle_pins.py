@@ -696,3 +696,21 @@ def test_ewald_beam_centre_reads_forward_scattering_and_trilinear_is_scipys():
                                         kf[..., 0].ravel() + n // 2], order=1, mode="nearest").reshape(val.shape)
     assert valid.sum() > 50
     assert np.allclose(val[valid], ref[valid], rtol=1e-12, atol=1e-15)
+
+
+def test_parity_count_helper_matches_brute_force():
+    """The helper behind the GPU two-voxel walk test (per-bin counts of all voxels and of the
+    kx-even ones, from the axes' k^2 histograms convolved by FFT) against a brute-force count
+    over every k of small grids, including an odd-radix edge."""
+    import math
+    from _cases import oracle_parity_counts
+    from paper_2303_13435_gb300 import inputs
+    for n, nb in [(32, 20), (64, 40), (126, 96)]:
+        dx = 0.04
+        edges = inputs.log_edges(2 * math.pi / (n * dx), math.pi / dx, nb)
+        even, total = oracle_parity_counts(n, dx, edges)
+        k = scatter.signed_freq(n)
+        kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+        j = scatter.bin_of_q(scatter.q_of_k2(kx ** 2 + ky ** 2 + kz ** 2, n, dx), edges)
+        assert np.array_equal(total, np.bincount(j[j >= 0], minlength=nb))
+        assert np.array_equal(even, np.bincount(j[(j >= 0) & (kx % 2 == 0)], minlength=nb))
